@@ -1,0 +1,97 @@
+"""CPU oracle for Hoshen-Kopelman labelling -- TEST INFRASTRUCTURE ONLY.
+
+The serial algorithm of Frijters, Krueger and Harting (CPC 2014), Sec. 2
+(raster scan, rules 1-3, label-of-labels list, final relabelling and
+compactification) plus the periodic edges of Sec. 3, written in plain C in
+``hk_oracle.c``.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  It does not import the CUDA package and the CUDA package never
+imports it.
+
+``label(phi, periodic)`` takes a C-contiguous float32 array of shape
+(nz, ny, nx) (x fastest) and returns ``(labels, sizes, hist, n_clusters)``:
+labels int32 (nz, ny, nx), each site's smallest row-major site index in its
+cluster or -1 on the medium; sizes int64[n_clusters] ordered by that index;
+hist int64[32] over floor(log2(size)).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hk_oracle.c")
+_LIB = os.path.join(_HERE, "libhk_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, ERR_ARG, ERR_TOO_LARGE, ERR_CAPACITY, ERR_NOMEM = 0, 1, 2, 3, 6
+
+
+def build(src: str = _SRC, out: str = _LIB, extra: tuple = ()) -> str:
+    """Compile the oracle with gcc (portable flags only: it runs on x86 and Arm)."""
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-Wall", "-Wextra", *extra, "-o", out, src]
+    subprocess.run(cmd, check=True)
+    return out
+
+
+def load(path: str | None = None):
+    """Load (building first if missing or older than the source) the oracle library."""
+    global _lib
+    with _lock:
+        if path is not None:
+            return _bind(ctypes.CDLL(path))
+        if _lib is None:
+            if not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+                build()
+            _lib = _bind(ctypes.CDLL(_LIB))
+        return _lib
+
+
+def _bind(lib):
+    f = lib.hk_oracle_label
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+    return lib
+
+
+def label(phi: np.ndarray, periodic=(1, 1, 1), sizes_cap: int | None = None, lib=None):
+    """Label ``phi`` (float32, shape (nz, ny, nx)) with the serial oracle."""
+    lib = lib or load()
+    phi = np.ascontiguousarray(phi, dtype=np.float32)
+    if phi.ndim != 3:
+        raise ValueError("phi must have shape (nz, ny, nx)")
+    nz, ny, nx = phi.shape
+    n = phi.size
+    if sizes_cap is None:
+        sizes_cap = (n + 1) // 2
+    labels = np.empty(phi.shape, dtype=np.int32)
+    sizes = np.zeros(max(int(sizes_cap), 1), dtype=np.int64)
+    hist = np.zeros(32, dtype=np.int64)
+    ncl = np.zeros(1, dtype=np.int64)
+    per = np.array([int(bool(p)) for p in periodic], dtype=np.int32)
+    rc = lib.hk_oracle_label(phi.ctypes.data, nx, ny, nz, per.ctypes.data, labels.ctypes.data,
+                             sizes.ctypes.data, int(sizes_cap), hist.ctypes.data, ncl.ctypes.data)
+    if rc not in (OK, ERR_CAPACITY):
+        raise RuntimeError(f"hk_oracle_label failed with status {rc}")
+    k = int(ncl[0])
+    return labels, sizes[:min(k, int(sizes_cap))].copy(), hist, k
+
+
+def status(phi: np.ndarray, periodic=(1, 1, 1), sizes_cap: int = 0, lib=None) -> int:
+    """Return the oracle's status code for a call (used by argument tests)."""
+    lib = lib or load()
+    phi = np.ascontiguousarray(phi, dtype=np.float32)
+    nz, ny, nx = phi.shape
+    labels = np.empty(phi.shape, dtype=np.int32)
+    sizes = np.zeros(max(sizes_cap, 1), dtype=np.int64)
+    hist = np.zeros(32, dtype=np.int64)
+    ncl = np.zeros(1, dtype=np.int64)
+    per = np.array([int(bool(p)) for p in periodic], dtype=np.int32)
+    return lib.hk_oracle_label(phi.ctypes.data, nx, ny, nz, per.ctypes.data, labels.ctypes.data,
+                               sizes.ctypes.data, int(sizes_cap), hist.ctypes.data, ncl.ctypes.data)

@@ -1,0 +1,212 @@
+/*
+ * hk_oracle.c -- serial Hoshen-Kopelman oracle.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+ * CPU definition that the CUDA path is checked against.  Only the test suite,
+ * the smoke check and the CPU-baseline leg of the benchmark may load it.  It
+ * shares no code, header, table or helper with the CUDA library: it declares
+ * its own entry points below and includes only the C standard library.
+ *
+ * What it computes (Frijters, Krueger, Harting, "Parallelised Hoshen-Kopelman
+ * algorithm for lattice-Boltzmann simulations", CPC 2014):
+ *
+ *   - Occupancy (Sec. 2, opening paragraph; Fig. 1 caption): a site x is part
+ *     of a cluster iff phi(x) > 0; phi <= 0 (and NaN) is the medium.
+ *   - Initialisation (Sec. 2; Fig. 1b): l(x) = 0 on the medium and l(x) = -1
+ *     ("to be labelled") on occupied sites.
+ *   - Raster scan (Sec. 2, Fig. 1c and the remark after the three rules): the
+ *     lattice is visited row by row (x fastest, then y, then z) and each site
+ *     looks only "backwards" at its face neighbours x-1, y-1, z-1; diagonal
+ *     sites are not neighbours.
+ *   - Rules 1-3 (Sec. 2, enumerated rules): no labelled neighbour -> a new
+ *     label l_max + 1; exactly one -> copy it; more than one -> take the
+ *     minimum of the neighbours' labels and store the equivalences between
+ *     them.
+ *   - Equivalence store (Sec. 3, tuning paragraph): a singly linked list of
+ *     label ids ("label of labels"), where following the list from any id ends
+ *     at the lowest id of its class; a new equivalence walks both lists to
+ *     their ends and re-points the end with the larger value at the smaller.
+ *   - Periodic boundaries (Sec. 3, Fig. 2 caption and the halo paragraph): the
+ *     paper merges across periodic edges through halo equivalences; serially
+ *     that is one extra equivalence for every occupied pair (n_a - 1, 0) along
+ *     each periodic axis a.  An axis of length 1 only has a self-edge.
+ *   - Relabelling and compactification (Sec. 2, final paragraph; Fig. 1g/h):
+ *     every id is reduced to the lowest id of its class, and the classes are
+ *     numbered 1..n in increasing order of that lowest id.
+ *   - Cluster sizes (Sec. 5, counting the sites with a given label) and the
+ *     droplet-size histogram (Fig. 5 caption), here binned by
+ *     floor(log2(size)).
+ *
+ * Output conventions (the readings listed in the design notes):
+ *   labels_out[s]  = the smallest row-major site index s = x + nx*(y + ny*z)
+ *                    of the cluster containing s, or -1 on the medium.  The
+ *                    lowest label id of a class is the one created at the
+ *                    class's first raster site, so this is the site at which
+ *                    that id was created.
+ *   sizes_out[k]   = number of sites of the cluster with compacted id k+1
+ *                    (clusters ordered by their smallest site index).
+ *   hist_out[b]    = number of clusters with floor(log2(size)) == b, b < 32.
+ *   n_clusters_out = number of clusters.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define HKO_OK 0
+#define HKO_ERR_ARG 1
+#define HKO_ERR_TOO_LARGE 2
+#define HKO_ERR_CAPACITY 3
+#define HKO_ERR_NOMEM 6
+
+int hk_oracle_label(const float *phi, int nx, int ny, int nz, const int periodic[3],
+                    int32_t *labels_out, int64_t *sizes_out, int64_t sizes_cap,
+                    int64_t *hist_out, int64_t *n_clusters_out);
+int hk_oracle_version(void);
+
+int hk_oracle_version(void) { return 1; }
+
+/* Growable per-label arrays: lol[k] (next id in k's equivalence list) and
+ * first[k] (the site at which id k was created).  Index 0 is unused, so that
+ * id k lives at index k and 0 keeps meaning "medium" as in the paper. */
+typedef struct {
+    int32_t *lol;
+    int64_t *first;
+    int64_t cap;
+} label_table;
+
+static int table_push(label_table *t, int32_t id, int64_t site) {
+    if (id >= t->cap) {
+        int64_t nc = t->cap ? 2 * t->cap : 1024;
+        while (nc <= id) nc *= 2;
+        int32_t *nl = (int32_t *)realloc(t->lol, (size_t)nc * sizeof(int32_t));
+        if (!nl) return HKO_ERR_NOMEM;
+        t->lol = nl;
+        int64_t *nf = (int64_t *)realloc(t->first, (size_t)nc * sizeof(int64_t));
+        if (!nf) return HKO_ERR_NOMEM;
+        t->first = nf;
+        t->cap = nc;
+    }
+    t->lol[id] = id; /* a new id is the end of its own list */
+    t->first[id] = site;
+    return HKO_OK;
+}
+
+/* Follow the linked list from id k to its end: the lowest id of k's class. */
+static int32_t list_end(const int32_t *lol, int32_t k) {
+    while (lol[k] != k) k = lol[k];
+    return k;
+}
+
+/* Record a == b: walk both lists to their ends and re-point the end with the
+ * larger value at the smaller one (Sec. 3, tuning paragraph). */
+static void store_equivalence(int32_t *lol, int32_t a, int32_t b) {
+    int32_t ea = list_end(lol, a);
+    int32_t eb = list_end(lol, b);
+    if (ea < eb) lol[eb] = ea;
+    else if (eb < ea) lol[ea] = eb;
+}
+
+int hk_oracle_label(const float *phi, int nx, int ny, int nz, const int periodic[3],
+                    int32_t *labels_out, int64_t *sizes_out, int64_t sizes_cap,
+                    int64_t *hist_out, int64_t *n_clusters_out) {
+    if (!phi || !periodic || !labels_out || !hist_out || !n_clusters_out) return HKO_ERR_ARG;
+    if (nx < 1 || ny < 1 || nz < 1 || sizes_cap < 0) return HKO_ERR_ARG;
+    if (sizes_cap > 0 && !sizes_out) return HKO_ERR_ARG;
+    const int64_t sx = 1, sy = nx, sz = (int64_t)nx * ny;
+    const int64_t N = (int64_t)nx * ny * nz;
+    if (N >= ((int64_t)1 << 31)) return HKO_ERR_TOO_LARGE;
+
+    /* The label field l(x) lives in labels_out until the final relabelling. */
+    int32_t *l = labels_out;
+
+    /* Initialisation: 0 on the medium, -1 on sites still to be labelled. */
+    for (int64_t s = 0; s < N; ++s) l[s] = (phi[s] > 0.0f) ? -1 : 0;
+
+    label_table t = {0, 0, 0};
+    int32_t l_max = 0;
+    int rc = HKO_OK;
+
+    /* Raster scan with rules 1-3, looking only at x-1, y-1 and z-1. */
+    for (int z = 0; z < nz && rc == HKO_OK; ++z) {
+        for (int y = 0; y < ny && rc == HKO_OK; ++y) {
+            for (int x = 0; x < nx; ++x) {
+                const int64_t s = x * sx + y * sy + z * sz;
+                if (l[s] != -1) continue;
+                int32_t nb[3];
+                int n_nb = 0;
+                if (x > 0 && l[s - sx] > 0) nb[n_nb++] = l[s - sx];
+                if (y > 0 && l[s - sy] > 0) nb[n_nb++] = l[s - sy];
+                if (z > 0 && l[s - sz] > 0) nb[n_nb++] = l[s - sz];
+                if (n_nb == 0) {                /* rule 1 */
+                    l_max += 1;
+                    rc = table_push(&t, l_max, s);
+                    if (rc != HKO_OK) break;
+                    l[s] = l_max;
+                } else if (n_nb == 1) {         /* rule 2 */
+                    l[s] = nb[0];
+                } else {                        /* rule 3 */
+                    int32_t m = nb[0];
+                    for (int i = 1; i < n_nb; ++i) if (nb[i] < m) m = nb[i];
+                    l[s] = m;
+                    for (int i = 0; i < n_nb; ++i)
+                        for (int j = i + 1; j < n_nb; ++j)
+                            store_equivalence(t.lol, nb[i], nb[j]);
+                }
+            }
+        }
+    }
+    if (rc != HKO_OK) { free(t.lol); free(t.first); return rc; }
+
+    /* Periodic edges: the pair (n_a - 1, 0) along every periodic axis. */
+    if (periodic[0] && nx >= 2)
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y) {
+                int64_t a = (nx - 1) * sx + y * sy + z * sz, b = y * sy + z * sz;
+                if (l[a] > 0 && l[b] > 0) store_equivalence(t.lol, l[a], l[b]);
+            }
+    if (periodic[1] && ny >= 2)
+        for (int z = 0; z < nz; ++z)
+            for (int x = 0; x < nx; ++x) {
+                int64_t a = x * sx + (ny - 1) * sy + z * sz, b = x * sx + z * sz;
+                if (l[a] > 0 && l[b] > 0) store_equivalence(t.lol, l[a], l[b]);
+            }
+    if (periodic[2] && nz >= 2)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                int64_t a = x * sx + y * sy + (nz - 1) * sz, b = x * sx + y * sy;
+                if (l[a] > 0 && l[b] > 0) store_equivalence(t.lol, l[a], l[b]);
+            }
+
+    /* Reduce every id to the lowest id of its class, then compactify: the
+     * classes get 1..n in increasing order of that lowest id. */
+    int32_t *compact = (int32_t *)malloc((size_t)(l_max + 1) * sizeof(int32_t));
+    int64_t *count = (int64_t *)calloc((size_t)l_max + 1, sizeof(int64_t));
+    if (!compact || !count) { free(compact); free(count); free(t.lol); free(t.first); return HKO_ERR_NOMEM; }
+    for (int32_t k = 1; k <= l_max; ++k) t.lol[k] = list_end(t.lol, k);
+    int32_t n = 0;
+    for (int32_t k = 1; k <= l_max; ++k) compact[k] = (t.lol[k] == k) ? ++n : compact[t.lol[k]];
+
+    /* Final pass over the lattice: apply the equivalences and count sites. */
+    for (int64_t s = 0; s < N; ++s) {
+        if (l[s] > 0) {
+            int32_t root = t.lol[l[s]];
+            count[compact[root]] += 1;
+            l[s] = (int32_t)t.first[root];
+        } else {
+            l[s] = -1;
+        }
+    }
+
+    memset(hist_out, 0, 32 * sizeof(int64_t));
+    for (int32_t c = 1; c <= n; ++c) {
+        int64_t size = count[c];
+        int b = 0;
+        while (((int64_t)2 << b) <= size) ++b;   /* floor(log2(size)) */
+        hist_out[b] += 1;
+        if (c - 1 < sizes_cap) sizes_out[c - 1] = size;
+    }
+    *n_clusters_out = n;
+
+    free(compact); free(count); free(t.lol); free(t.first);
+    return (n > sizes_cap) ? HKO_ERR_CAPACITY : HKO_OK;
+}

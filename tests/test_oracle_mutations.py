@@ -1,0 +1,101 @@
+"""Planted mistakes: the pins must reject every plausible slip in the oracle.
+
+Each case copies ``oracle/hk_oracle.c``, applies one textual mutation (a dropped
+term, a wrong sign or index, a swapped operand), compiles the copy to a
+temporary library on the CPU and runs a fast battery of the pins from
+``test_oracle_pins.py``.  The battery must fail for every mutant and pass for
+the unmodified source.
+"""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from brute import bfs_label, log2_hist
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "hk_oracle.c")
+
+MUTATIONS = {
+    "drop_z_neighbour": ("if (z > 0 && l[s - sz] > 0) nb[n_nb++] = l[s - sz];", ""),
+    "drop_y_neighbour": ("if (y > 0 && l[s - sy] > 0) nb[n_nb++] = l[s - sy];", ""),
+    # (taking the max instead of the min in rule 3 is an equivalent mutant: the final
+    # relabelling reduces every id to its class minimum, so it is not listed)
+    "rule3_first_pair_only": ("for (int j = i + 1; j < n_nb; ++j)", "for (int j = i + 1; j < 2; ++j)"),
+    "rule3_no_equivalence": ("store_equivalence(t.lol, nb[i], nb[j]);", "(void)j;"),
+    "link_larger_end_wrong_way": ("if (ea < eb) lol[eb] = ea;", "if (ea < eb) lol[ea] = eb;"),
+    "occupancy_ge": ("(phi[s] > 0.0f) ? -1 : 0", "(phi[s] >= 0.0f) ? -1 : 0"),
+    "drop_x_wrap": ("if (periodic[0] && nx >= 2)", "if (0)"),
+    "drop_z_wrap": ("if (periodic[2] && nz >= 2)", "if (0)"),
+    "wrap_off_by_one": ("int64_t a = x * sx + (ny - 1) * sy + z * sz", "int64_t a = x * sx + (ny - 2) * sy + z * sz"),
+    "wrap_axis_swapped": ("if (periodic[1] && ny >= 2)", "if (periodic[0] && ny >= 2)"),
+    "hist_off_by_one": ("while (((int64_t)2 << b) <= size) ++b;", "while (((int64_t)1 << b) <= size) ++b;"),
+    "label_is_compact_id": ("l[s] = (int32_t)t.first[root];", "l[s] = compact[root];"),
+    "sizes_shifted": ("if (c - 1 < sizes_cap) sizes_out[c - 1] = size;",
+                      "if (c - 1 < sizes_cap) sizes_out[(c % n)] = size;"),
+    "raster_y_stride": ("const int64_t sx = 1, sy = nx, sz = (int64_t)nx * ny;",
+                        "const int64_t sx = 1, sy = ny, sz = (int64_t)nx * ny;"),
+}
+
+
+def battery(lib):
+    """Fast subset of the pins; raises AssertionError on the first disagreement."""
+    def lab(occ, per):
+        return oracle.label(np.where(occ, 1.0, -1.0).astype(np.float32), per, lib=lib)
+
+    def same(got, want):
+        assert got[3] == want[3]
+        np.testing.assert_array_equal(got[0], want[0])
+        np.testing.assert_array_equal(got[1], want[1])
+        np.testing.assert_array_equal(got[2], want[2])
+
+    pers = list(itertools.product((0, 1), repeat=3))
+    for bits in range(256):
+        occ = np.array([(bits >> i) & 1 for i in range(8)], dtype=bool).reshape(2, 2, 2)
+        for per in pers:
+            same(lab(occ, per), bfs_label(occ, per))
+    rng = np.random.default_rng(5)
+    for _ in range(30):
+        shape = tuple(int(v) for v in rng.integers(1, 7, size=3))
+        occ = rng.random(shape) < rng.uniform(0.2, 0.8)
+        for per in pers:
+            same(lab(occ, per), bfs_label(occ, per))
+    # non-square shapes with distinct axis lengths
+    for shape in [(3, 5, 7), (7, 3, 5), (4, 6, 9)]:
+        occ = rng.random(shape) < 0.55
+        for per in pers:
+            same(lab(occ, per), bfs_label(occ, per))
+    # occupancy rule on signed zeros
+    phi = np.array([0.0, -0.0, 1.0, 0.0], dtype=np.float32).reshape(1, 1, 4)
+    got = oracle.label(phi, (0, 0, 0), lib=lib)
+    assert got[3] == 1 and got[0].reshape(-1).tolist() == [-1, -1, 2, -1]
+    # histogram of a known size set: clusters of sizes 1, 2, 3, 4 along a row
+    row = np.array([1, 0, 1, 1, 0, 1, 1, 1, 0, 1, 1, 1, 1], dtype=bool).reshape(1, 1, 13)
+    got = lab(row, (0, 0, 0))
+    assert got[1].tolist() == [1, 2, 3, 4]
+    np.testing.assert_array_equal(got[2], log2_hist([1, 2, 3, 4]))
+
+
+def _build(tmp_path, name, mutation):
+    text = open(SRC).read()
+    if mutation is not None:
+        old, new = mutation
+        assert text.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+        text = text.replace(old, new)
+    src = tmp_path / f"{name}.c"
+    src.write_text(text)
+    out = tmp_path / f"lib{name}.so"
+    oracle.build(str(src), str(out), extra=("-w",))
+    return oracle.load(str(out))
+
+
+def test_unmutated_passes(tmp_path):
+    battery(_build(tmp_path, "clean", None))
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_mutant_is_caught(tmp_path, name):
+    lib = _build(tmp_path, name, MUTATIONS[name])
+    with pytest.raises(AssertionError):
+        battery(lib)
