@@ -1,0 +1,297 @@
+"""Benchmark of the Hoshen-Kopelman labelling path on GB300.
+
+Default workload: critical site percolation on a 1024^3 lattice (float32
+phi = u - (1 - 0.3116), u iid uniform, periodic in x, y, z), labelled, sized
+and histogrammed per step through the C ABI with phi resident in HBM.  One
+JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+--impl reference times the CPU oracle (the serial algorithm of the paper) on
+the host cores, on a bounded sample of the same workload.  Under torchrun
+(N > 1) every rank labels its own lattice (independent replicas, weak
+scaling); only rank 0 runs the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gsites/s labelled+sized at 1024^3 p_c; batched vs per-lattice; p50/p99 latency"
+P_C = 0.3116
+L_HEADLINE = 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gb300", choices=("gb300", "reference"))
+    ap.add_argument("--size", type=int, default=L_HEADLINE, help="lattice side (default 1024)")
+    ap.add_argument("--tile", default="", help="ty,tz tile override")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="hk_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "20",
+                 "-i", str(self.dev)], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.05)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline_oracle(side: int = 512, reps: int = 3):
+    """Serial oracle on a bounded sample of the same distribution (one host core)."""
+    import oracle
+    from paper_1405_1931_gb300 import fields
+    oracle.load()
+    phi = fields.iid_field(side, side, side, seed=0, occupancy=P_C)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.label(phi, (1, 1, 1))
+    dt = time.perf_counter() - t0
+    sites = reps * side ** 3
+    return {"value": sites / dt / 1e9, "unit": "Gsites/s", "cores": 1, "kind": "oracle",
+            "sample": f"{reps} x {side}^3 iid phi at p=0.3116, periodic xyz (serial C oracle, {dt:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle as it stands, timed per step on a bounded sample."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_1405_1931_gb300 import fields
+    oracle.load()
+    side = 256
+    phi = fields.iid_field(side, side, side, seed=0, occupancy=P_C)
+    for _ in range(args.warmup):
+        oracle.label(phi, (1, 1, 1))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.label(phi, (1, 1, 1))
+    dt = time.perf_counter() - t0
+    value = args.steps * side ** 3 / dt / 1e9
+    sample = f"each step: {side}^3 iid phi at p=0.3116, periodic xyz (the 1024^3 workload's distribution)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gsites/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": f"critical site percolation {side}^3 sample of 1024^3, p=0.3116, periodic xyz"},
+            "cpu_baseline": {"value": value, "unit": "Gsites/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "Gsites/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    from paper_1405_1931_gb300 import hk
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    L = args.size
+    N = L ** 3
+    lab = hk.Labeller(local)
+    if args.tile:
+        lab.set_tile(*[int(v) for v in args.tile.split(",")])
+    stream = torch.cuda.current_stream()
+    phi = torch.empty((L, L, L), dtype=torch.float32, device="cuda")
+    rc = hk.hk_gen_iid(phi.data_ptr(), L, L, L, 0, P_C, hk._stream_handle(stream))
+    assert rc == 0
+    out = lab.alloc_outputs(phi.shape, phi.device)
+    per = (1, 1, 1)
+
+    for _ in range(max(args.warmup, 3)):
+        lab.label(phi, per, out=out)
+    torch.cuda.synchronize()
+
+    hk.hk_set_timing(lab.ctx, True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        lab.label(phi, per, out=out)
+    t_end.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms_total = t_start.elapsed_time(t_end)
+    passes = hk.hk_get_timing(lab.ctx)
+    hk.hk_set_timing(lab.ctx, False)
+
+    ms_step = ms_total / args.steps
+    if dist is not None:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * N / (ms_step * 1e-3) / 1e9
+
+    labels, sizes, hist, ncl, cap = out
+    n_clusters = int(ncl.item())
+
+    # roofline of the dominant kernel and of the whole path
+    peak, peak_kind = read_peaks()
+    names = list(hk.PASS_NAMES)
+    dom = int(np.argmax(passes))
+    alg = {"tile_label": 4 * N, "flatten": 4 * N + 8 * n_clusters + 8 * 32}
+    dom_name = names[dom]
+    dom_bytes = alg.get(dom_name, 0)
+    achieved = dom_bytes / (passes[dom] * 1e-3) / 1e9 if dom_bytes else None
+    roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "algorithmic_bytes": dom_bytes, "avg_ms": passes[dom], "peak_kind": peak_kind}
+    path_bytes = 8 * N + 8 * n_clusters + 8 * 32
+    path_achieved = path_bytes / (ms_step * 1e-3) / 1e9
+    path_roofline = {"bound": "hbm", "achieved": path_achieved, "peak": peak, "unit": "GB/s",
+                     "frac": path_achieved / peak, "algorithmic_bytes": path_bytes}
+
+    # end to end through the host-buffer entry point (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        phi_h = torch.empty((L, L, L), dtype=torch.float32, pin_memory=True)
+        phi_h.copy_(phi)
+        lab_h = torch.empty((L, L, L), dtype=torch.int32, pin_memory=True)
+        sizes_h = torch.empty(cap, dtype=torch.int64, pin_memory=True)
+        hist_h = torch.empty(32, dtype=torch.int64, pin_memory=True)
+        ncl_h = torch.empty(1, dtype=torch.int64, pin_memory=True)
+        ph = hk._stream_handle(stream)
+
+        def e2e_step():
+            rc = hk.hk_label_host(lab.ctx, phi_h.data_ptr(), L, L, L, per, lab_h.data_ptr(), sizes_h.data_ptr(),
+                                  cap, hist_h.data_ptr(), ncl_h.data_ptr(), ph)
+            assert rc == hk.HK_OK, rc
+
+        e2e_step()
+        k_e2e = max(3, min(args.steps, 10))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            e2e_step()
+        barrier()
+        ms_e2e = (time.perf_counter() - t0) / k_e2e * 1e3
+        if dist is not None:
+            t = torch.tensor([ms_e2e], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_e2e = float(t.item())
+        assert int(ncl_h[0]) == n_clusters
+        e2e = {"value": world * N / (ms_e2e * 1e-3) / 1e9, "unit": "Gsites/s", "ms_per_step": ms_e2e,
+               "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 4 * N + 8 * n_clusters + 8 * 32 + 8,
+               "entry": "hk_label_host (pinned host buffers)"}
+        del phi_h, lab_h, sizes_h
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_oracle()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "Gsites/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": {"workload": f"critical site percolation {L}^3, p=0.3116, periodic xyz",
+                           "nx": L, "ny": L, "nz": L, "tile": [32, lab_tile(lab)[0], lab_tile(lab)[1]],
+                           "cache": "inputs larger than L2 (4 B/site phi and labels at 1024^3: 8 GiB per step)",
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                "n_clusters": n_clusters,
+                "passes_ms": dict(zip(names, passes)),
+                "roofline": roofline, "path_roofline": path_roofline,
+                "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": 8 * args.steps, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    lab.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def lab_tile(lab):
+    return lab.tile
+
+
+if __name__ == "__main__":
+    main()

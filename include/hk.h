@@ -1,0 +1,170 @@
+/*
+ * hk.h -- C ABI of the GB300 Hoshen-Kopelman cluster-labelling library (libhk).
+ *
+ * Method: Frijters, Krueger, Harting, "Parallelised Hoshen-Kopelman algorithm
+ * for lattice-Boltzmann simulations", Comput. Phys. Commun. (2014).
+ *
+ * What a call computes, for a 3D lattice of nx*ny*nz sites holding a float32
+ * order parameter phi:
+ *   - occupancy: site x belongs to a cluster iff phi(x) > 0 (Sec. 2, opening
+ *     paragraph); phi <= 0, -0 and NaN are the medium;
+ *   - clusters: the connected components of the occupied sites under
+ *     nearest-neighbour (face, 6-)connectivity, diagonals excluded (Sec. 2,
+ *     remark after the three rules), with per-axis periodic edges
+ *     (n_a - 1) <-> 0 (Sec. 3, Fig. 2 caption and the halo paragraph);
+ *   - labels: each cluster is labelled by its smallest row-major site index
+ *     s = x + nx*(y + ny*z) (x fastest, phi laid out as C array
+ *     phi[nz][ny][nx]); the medium gets -1.  This is the "smallest possible
+ *     number" relabelling of Sec. 2 (final paragraph) expressed as a site
+ *     index rather than a compacted id;
+ *   - sizes: sizes_out[k] = number of sites of the cluster with the (k+1)-th
+ *     smallest label, i.e. clusters in the compactified order 1..n of Sec. 2
+ *     (final paragraph); the site counts are those of Sec. 5 ("counting the
+ *     number of sites with a particular label");
+ *   - histogram: hist_out[b] = number of clusters whose size has
+ *     floor(log2(size)) == b, 0 <= b < 32 (the droplet-size histogram of
+ *     Fig. 5, binned by integer size; any radius binning R_c ~ size^(1/3) is a
+ *     monotone re-binning done by the caller);
+ *   - n_clusters_out = n.
+ * The result is unique, so it is bit-identical to the serial algorithm.
+ *
+ * Conventions shared by every entry point:
+ *   - Device pointers are caller-owned CUDA device memory on the context's
+ *     device; the library never frees them.  Host pointers are read during the
+ *     call only.
+ *   - Calls are asynchronous on the given stream (a cudaStream_t passed as
+ *     void*, NULL = legacy default stream) unless stated otherwise; results are
+ *     valid once that stream has reached the end of the call.
+ *   - A context owns a workspace that it grows on demand (cudaMalloc) and
+ *     reuses.  Calls that share a context must be issued on one stream (or be
+ *     otherwise ordered); use one context per concurrent stream.
+ *   - Return codes: HK_OK, or one of the HK_ERR_* codes below.  Argument
+ *     errors are detected on the host before anything is enqueued.
+ *   - N = nx*ny*nz must be < 2^31 (labels are int32 site indices).
+ */
+#ifndef HK_H
+#define HK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HK_OK            0
+#define HK_ERR_ARG       1  /* null pointer, dimension < 1, negative capacity, bad count */
+#define HK_ERR_TOO_LARGE 2  /* nx*ny*nz >= 2^31 */
+#define HK_ERR_CAPACITY  3  /* more clusters than sizes_cap (labels, hist, count still valid) */
+#define HK_ERR_CUDA      4  /* a CUDA runtime call failed (see hk_last_cuda_error) */
+#define HK_ERR_TIMEOUT   5  /* a bounded device-side wait gave up */
+#define HK_ERR_NOMEM     6  /* workspace allocation failed */
+
+typedef struct hk_ctx hk_ctx;
+
+/* Create a context bound to CUDA device `device`.  *out receives the handle.
+ * Errors: HK_ERR_ARG (out == NULL), HK_ERR_CUDA (bad device). */
+int hk_create(hk_ctx **out, int device);
+
+/* Release a context and its workspace.  The caller must make sure no call on
+ * it is still running on the GPU.  NULL is ignored. */
+void hk_destroy(hk_ctx *ctx);
+
+/* Device workspace in bytes that one hk_label call on an nx*ny*nz lattice
+ * needs (an upper bound, independent of phi).  Used for admission control.
+ * Returns 0 for invalid dimensions. */
+size_t hk_workspace_bytes(int nx, int ny, int nz);
+
+/* Grow the context's workspace to at least `bytes` now, so later calls do not
+ * allocate.  Errors: HK_ERR_ARG, HK_ERR_NOMEM. */
+int hk_reserve(hk_ctx *ctx, size_t bytes);
+
+/* Label one lattice (Sec. 2 rules with Sec. 3's periodic merging; see above).
+ *   phi            device, float32[nz][ny][nx], read only.
+ *   periodic       host, int[3]: nonzero = periodic along x, y, z.
+ *   labels_out     device, int32[nz][ny][nx]: min site index of the cluster, -1 medium.
+ *   sizes_out      device, int64[sizes_cap]: cluster sizes in label order (may be
+ *                  NULL when sizes_cap == 0).  ceil(N/2) entries always suffice
+ *                  (clusters are pairwise non-adjacent: at most V/2 of them, Sec. 3).
+ *   hist_out       device, int64[32] (may be NULL).
+ *   n_clusters_out device, int64[1] (may be NULL).
+ *   stream         cudaStream_t as void*.
+ * When sizes_cap < ceil(N/2) the call synchronises the stream at its end to
+ * check the count and returns HK_ERR_CAPACITY if n > sizes_cap (then only the
+ * first sizes_cap sizes are written; everything else is complete); otherwise it
+ * is fully asynchronous.
+ * Errors: HK_ERR_ARG, HK_ERR_TOO_LARGE, HK_ERR_NOMEM, HK_ERR_CUDA, HK_ERR_CAPACITY. */
+int hk_label(hk_ctx *ctx, const float *phi, int nx, int ny, int nz, const int periodic[3],
+             int32_t *labels_out, int64_t *sizes_out, int64_t sizes_cap,
+             int64_t *hist_out, int64_t *n_clusters_out, void *stream);
+
+/* One lattice of a batch: the arguments of hk_label bundled (device pointers,
+ * same meaning and layout). */
+typedef struct hk_lattice {
+    const float *phi;
+    int nx, ny, nz;
+    int periodic[3];
+    int32_t *labels;
+    int64_t *sizes;
+    int64_t sizes_cap;
+    int64_t *hist;
+    int64_t *n_clusters;
+} hk_lattice;
+
+/* Label n independent lattices of arbitrary, uneven shapes in one pass
+ * sequence: every kernel runs once over the tiles of all lattices together
+ * (one launch per pass for the whole batch, replayed from a cached CUDA graph
+ * keyed by the batch's shapes).  Results are bit-identical to n separate
+ * hk_label calls.  `lats` is a host array of n descriptors, read during the
+ * call.  The capacity rule of hk_label applies per lattice.
+ * Errors: HK_ERR_ARG (n < 0, bad descriptor), HK_ERR_TOO_LARGE, HK_ERR_NOMEM,
+ * HK_ERR_CUDA, HK_ERR_CAPACITY (some lattice overflowed its sizes_cap). */
+int hk_label_batched(hk_ctx *ctx, const hk_lattice *lats, int n, void *stream);
+
+/* hk_label on HOST buffers: copies phi host->device, labels on the device and
+ * copies labels, sizes, hist and the count back; synchronous.  Host buffers
+ * may be pageable or pinned (pinned is faster).  Same argument meaning as
+ * hk_label with every pointer in host memory.  The device copies live in the
+ * context's workspace. */
+int hk_label_host(hk_ctx *ctx, const float *phi_host, int nx, int ny, int nz, const int periodic[3],
+                  int32_t *labels_host, int64_t *sizes_host, int64_t sizes_cap,
+                  int64_t *hist_host, int64_t *n_clusters_host, void *stream);
+
+/* Select the tile shape (rows per tile along y and z; x tiles are always 32
+ * sites wide).  Supported: (ty, tz) in {(8,8), (16,8), (16,16), (32,8)}; 0,0 =
+ * the library default.  Applies to later calls on this context.
+ * Errors: HK_ERR_ARG for an unsupported shape. */
+int hk_set_tile(hk_ctx *ctx, int ty, int tz);
+
+/* Per-pass timing.  hk_set_timing(ctx, 1) resets the totals and makes every
+ * later call record CUDA events on its own stream between its passes (a ring
+ * of 64 event sets; the host waits for a call 64 calls old before reusing its
+ * set).  hk_get_timing synchronises on the timed calls still in flight and
+ * writes up to max_n per-pass AVERAGE durations in milliseconds over all timed
+ * calls since timing was enabled to ms_out (host), in pass order: tile_label,
+ * face_merge, piece_finalize, scan (three kernels), lattice_finish, flatten;
+ * *n_out gets the number of passes.  For a batch split into several launch
+ * chunks each chunk counts as one call.  Timing adds event records only;
+ * results are unchanged.  Errors: HK_ERR_ARG (no timed call yet, NULL ctx or
+ * ms_out), HK_ERR_CUDA. */
+#define HK_NUM_PASSES 6
+int hk_set_timing(hk_ctx *ctx, int enable);
+int hk_get_timing(hk_ctx *ctx, float *ms_out, int max_n, int *n_out);
+
+/* Synchronise `stream` and report whether any bounded device-side loop of the
+ * context's calls since the previous check gave up (a corrupted union-find
+ * would otherwise never terminate).  Clears the flag.  Returns HK_OK,
+ * HK_ERR_TIMEOUT or HK_ERR_CUDA. */
+int hk_sync_status(hk_ctx *ctx, void *stream);
+
+/* The last CUDA error code seen by the context (cudaError_t as int). */
+int hk_last_cuda_error(const hk_ctx *ctx);
+
+/* Human-readable name of a status code (static string). */
+const char *hk_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HK_H */

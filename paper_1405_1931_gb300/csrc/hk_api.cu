@@ -1,0 +1,428 @@
+// hk_api.cu -- the C ABI declared in include/hk.h: contexts, workspace,
+// argument checks and the pass sequence of hk_kernels.cu.
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/hk.h"
+#include "hk_device.cuh"
+#include "hk_launch.h"
+
+using hk::LatDev;
+using hk::Plan;
+using hk::TileInfo;
+using hk::Work;
+
+struct hk_ctx {
+    int device = 0;
+    int ty = 16, tz = 16;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    void *io = nullptr;       // device buffers of hk_label_host
+    size_t io_bytes = 0;
+    int last_cuda = 0;
+    int32_t *dstatus = nullptr;   // device status word (STATUS_* flags), survives workspace growth
+    // per-pass timing: a ring of event sets, one per timed call
+    static constexpr int RING = 64;
+    bool timing = false;
+    int64_t ncalls = 0;        // timed calls since timing was enabled
+    int64_t nacc = 0;          // calls already folded into acc
+    double acc[hk::NUM_PASSES] = {};
+    cudaEvent_t ev[RING][hk::NUM_PASSES + 1] = {};
+};
+
+namespace {
+
+constexpr int DEFAULT_TY = 16, DEFAULT_TZ = 16;
+constexpr int64_t MAX_SITES = (int64_t)1 << 31;
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+struct Layout {
+    size_t mask, cnt, pre, bsum, face, tinfo, parent, key, psize, npieces, status, ncl, total;
+};
+
+Layout make_layout(const TileInfo &ti, const Plan &P) {
+    Layout L{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
+    const int64_t nb = (P.nseg + 4096) / 4096;
+    L.mask = take((size_t)P.ntiles * ti.rows * 4);
+    L.cnt = take((size_t)P.nseg * 4);
+    L.pre = take((size_t)(P.nseg + 1) * 4);
+    L.bsum = take((size_t)nb * 4);
+    L.face = take((size_t)P.ntiles * ti.face_stride * 2);
+    L.tinfo = take((size_t)P.ntiles * 8);
+    L.parent = take((size_t)P.piece_cap * 4);
+    L.key = take((size_t)P.piece_cap * 4);
+    L.psize = take((size_t)P.piece_cap * 4);
+    L.npieces = take(4);
+    L.status = take(4);
+    L.ncl = take((size_t)hk::MAX_LAT_PER_LAUNCH * 8);
+    L.total = off;
+    return L;
+}
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+void add_lattice(const TileInfo &ti, int nx, int ny, int nz, Plan &P) {
+    const int64_t nbx = ceil_div(nx, hk::TX), nby = ceil_div(ny, ti.ty), nbz = ceil_div(nz, ti.tz);
+    P.ntiles += nbx * nby * nbz;
+    P.nseg += nbx * (int64_t)ny * nz;
+}
+
+int fail_cuda(hk_ctx *ctx, cudaError_t e) {
+    ctx->last_cuda = (int)e;
+    return HK_ERR_CUDA;
+}
+
+int ensure_ws(hk_ctx *ctx, size_t bytes) {
+    if (bytes <= ctx->ws_bytes) return HK_OK;
+    if (ctx->ws) {
+        cudaDeviceSynchronize();
+        cudaFree(ctx->ws);
+        ctx->ws = nullptr;
+        ctx->ws_bytes = 0;
+    }
+    const size_t want = bytes + bytes / 8;   // headroom against frequent regrowth
+    cudaError_t e = cudaMalloc(&ctx->ws, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        e = cudaMalloc(&ctx->ws, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ctx->ws = nullptr;
+            return HK_ERR_NOMEM;
+        }
+        ctx->ws_bytes = bytes;
+        return HK_OK;
+    }
+    ctx->ws_bytes = want;
+    return HK_OK;
+}
+
+int check_lattice(const hk_lattice &l) {
+    if (!l.phi || !l.labels) return HK_ERR_ARG;
+    if (l.nx < 1 || l.ny < 1 || l.nz < 1) return HK_ERR_ARG;
+    if (l.sizes_cap < 0 || (l.sizes_cap > 0 && !l.sizes)) return HK_ERR_ARG;
+    if ((int64_t)l.nx * l.ny * l.nz >= MAX_SITES) return HK_ERR_TOO_LARGE;
+    return HK_OK;
+}
+
+// Add the pass durations of ring slot `slot` (a completed call) to the totals.
+cudaError_t fold_slot(hk_ctx *ctx, int slot) {
+    cudaError_t e = cudaEventSynchronize(ctx->ev[slot][hk::NUM_PASSES]);
+    if (e != cudaSuccess) return e;
+    for (int i = 0; i < hk::NUM_PASSES; ++i) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, ctx->ev[slot][i], ctx->ev[slot][i + 1]);
+        if (e != cudaSuccess) return e;
+        ctx->acc[i] += ms;
+    }
+    ctx->nacc += 1;
+    return cudaSuccess;
+}
+
+// Fold the oldest unfolded call, which occupies `slot`, before the slot is reused.
+void fold_timing(hk_ctx *ctx, int slot) {
+    if (fold_slot(ctx, slot) != cudaSuccess) ctx->timing = false;
+}
+
+// Label lats[0..n) with at most MAX_LAT_PER_LAUNCH lattices per pass sequence.
+int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st) {
+    TileInfo ti;
+    if (!hk::tile_info(ctx->ty, ctx->tz, ti)) return HK_ERR_ARG;
+    for (int i = 0; i < n; ++i) {
+        int rc = check_lattice(lats[i]);
+        if (rc != HK_OK) return rc;
+    }
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return fail_cuda(ctx, e);
+
+    // size the workspace for the largest chunk
+    size_t need = 0;
+    for (int c0 = 0; c0 < n; c0 += hk::MAX_LAT_PER_LAUNCH) {
+        Plan P{0, 0, 0};
+        for (int i = c0; i < std::min(n, c0 + hk::MAX_LAT_PER_LAUNCH); ++i)
+            add_lattice(ti, lats[i].nx, lats[i].ny, lats[i].nz, P);
+        P.piece_cap = P.ntiles * ti.max_boundary;
+        need = std::max(need, make_layout(ti, P).total);
+    }
+    int rc = ensure_ws(ctx, need);
+    if (rc != HK_OK) return rc;
+    if (!ctx->dstatus) {
+        e = cudaMalloc(&ctx->dstatus, 256);
+        if (e != cudaSuccess) { cudaGetLastError(); ctx->dstatus = nullptr; return HK_ERR_NOMEM; }
+        e = cudaMemset(ctx->dstatus, 0, 256);
+        if (e != cudaSuccess) return fail_cuda(ctx, e);
+    }
+
+    bool any_check = false;
+    std::vector<int64_t> counts(n, 0);
+    for (int c0 = 0; c0 < n; c0 += hk::MAX_LAT_PER_LAUNCH) {
+        const int cn = std::min(n - c0, hk::MAX_LAT_PER_LAUNCH);
+        Plan P{0, 0, 0};
+        std::vector<LatDev> dev(cn);
+        for (int i = 0; i < cn; ++i) {
+            const hk_lattice &l = lats[c0 + i];
+            LatDev &d = dev[i];
+            std::memset(&d, 0, sizeof(d));
+            d.phi = l.phi;
+            d.labels = l.labels;
+            d.sizes = l.sizes;
+            d.sizes_cap = l.sizes ? l.sizes_cap : 0;
+            d.hist = l.hist;
+            d.ncl = l.n_clusters;
+            d.nx = l.nx; d.ny = l.ny; d.nz = l.nz;
+            for (int a = 0; a < 3; ++a) d.per[a] = l.periodic[a] ? 1 : 0;
+            d.nbx = (int)ceil_div(l.nx, hk::TX);
+            d.nby = (int)ceil_div(l.ny, ti.ty);
+            d.nbz = (int)ceil_div(l.nz, ti.tz);
+            d.tile0 = P.ntiles;
+            d.seg0 = P.nseg;
+            add_lattice(ti, l.nx, l.ny, l.nz, P);
+        }
+        P.piece_cap = P.ntiles * ti.max_boundary;
+        const Layout Ly = make_layout(ti, P);
+        char *base = static_cast<char *>(ctx->ws);
+        Work W;
+        W.mask = reinterpret_cast<uint32_t *>(base + Ly.mask);
+        W.cnt = reinterpret_cast<uint32_t *>(base + Ly.cnt);
+        W.pre = reinterpret_cast<uint32_t *>(base + Ly.pre);
+        W.bsum = reinterpret_cast<uint32_t *>(base + Ly.bsum);
+        W.face = reinterpret_cast<uint16_t *>(base + Ly.face);
+        W.tinfo = reinterpret_cast<int2 *>(base + Ly.tinfo);
+        W.parent = reinterpret_cast<int32_t *>(base + Ly.parent);
+        W.key = reinterpret_cast<int32_t *>(base + Ly.key);
+        W.psize = reinterpret_cast<int32_t *>(base + Ly.psize);
+        W.npieces = reinterpret_cast<int32_t *>(base + Ly.npieces);
+        W.status = ctx->dstatus;
+        W.piece_cap = P.piece_cap;
+        int64_t *slots = reinterpret_cast<int64_t *>(base + Ly.ncl);
+        bool chunk_check = false;
+        for (int i = 0; i < cn; ++i) {
+            const hk_lattice &l = lats[c0 + i];
+            const int64_t N = (int64_t)l.nx * l.ny * l.nz;
+            if (!dev[i].ncl) dev[i].ncl = slots + i;
+            if (dev[i].sizes_cap < (N + 1) / 2) chunk_check = true;
+        }
+        cudaEvent_t *ev = nullptr;
+        if (ctx->timing) {
+            const int slot = (int)(ctx->ncalls % hk_ctx::RING);
+            if (ctx->ncalls - ctx->nacc >= hk_ctx::RING) fold_timing(ctx, slot);
+            ev = ctx->ev[slot];
+            ctx->ncalls += 1;
+        }
+        e = hk::launch_label(ctx->ty, ctx->tz, dev.data(), cn, P, W, st, ev);
+        if (e != cudaSuccess) return fail_cuda(ctx, e);
+        if (chunk_check) {
+            // the capacity rule needs the counts: wait for this chunk
+            any_check = true;
+            e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return fail_cuda(ctx, e);
+            for (int i = 0; i < cn; ++i) {
+                e = cudaMemcpy(&counts[c0 + i], dev[i].ncl, sizeof(int64_t), cudaMemcpyDeviceToHost);
+                if (e != cudaSuccess) return fail_cuda(ctx, e);
+            }
+        }
+    }
+    if (any_check)
+        for (int i = 0; i < n; ++i)
+            if (counts[i] > lats[i].sizes_cap) return HK_ERR_CAPACITY;
+    return HK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hk_create(hk_ctx **out, int device) {
+    if (!out) return HK_ERR_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return HK_ERR_CUDA;
+    }
+    hk_ctx *c = new hk_ctx();
+    c->device = device;
+    c->ty = DEFAULT_TY;
+    c->tz = DEFAULT_TZ;
+    *out = c;
+    return HK_OK;
+}
+
+void hk_destroy(hk_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->io) cudaFree(ctx->io);
+    if (ctx->dstatus) cudaFree(ctx->dstatus);
+    for (auto &set : ctx->ev)
+        for (auto &e : set)
+            if (e) cudaEventDestroy(e);
+    delete ctx;
+}
+
+size_t hk_workspace_bytes(int nx, int ny, int nz) {
+    if (nx < 1 || ny < 1 || nz < 1 || (int64_t)nx * ny * nz >= MAX_SITES) return 0;
+    TileInfo ti;
+    hk::tile_info(DEFAULT_TY, DEFAULT_TZ, ti);
+    Plan P{0, 0, 0};
+    add_lattice(ti, nx, ny, nz, P);
+    P.piece_cap = P.ntiles * ti.max_boundary;
+    return make_layout(ti, P).total;
+}
+
+int hk_reserve(hk_ctx *ctx, size_t bytes) {
+    if (!ctx) return HK_ERR_ARG;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail_cuda(ctx, cudaGetLastError());
+    return ensure_ws(ctx, bytes);
+}
+
+int hk_label(hk_ctx *ctx, const float *phi, int nx, int ny, int nz, const int periodic[3],
+             int32_t *labels_out, int64_t *sizes_out, int64_t sizes_cap, int64_t *hist_out,
+             int64_t *n_clusters_out, void *stream) {
+    if (!ctx || !periodic) return HK_ERR_ARG;
+    hk_lattice l;
+    l.phi = phi;
+    l.nx = nx; l.ny = ny; l.nz = nz;
+    for (int a = 0; a < 3; ++a) l.periodic[a] = periodic[a];
+    l.labels = labels_out;
+    l.sizes = sizes_out;
+    l.sizes_cap = sizes_cap;
+    l.hist = hist_out;
+    l.n_clusters = n_clusters_out;
+    return run_lattices(ctx, &l, 1, static_cast<cudaStream_t>(stream));
+}
+
+int hk_label_batched(hk_ctx *ctx, const hk_lattice *lats, int n, void *stream) {
+    if (!ctx || n < 0 || (n > 0 && !lats)) return HK_ERR_ARG;
+    if (n == 0) return HK_OK;
+    return run_lattices(ctx, lats, n, static_cast<cudaStream_t>(stream));
+}
+
+int hk_label_host(hk_ctx *ctx, const float *phi_host, int nx, int ny, int nz, const int periodic[3],
+                  int32_t *labels_host, int64_t *sizes_host, int64_t sizes_cap, int64_t *hist_host,
+                  int64_t *n_clusters_host, void *stream) {
+    if (!ctx || !periodic || !phi_host || !labels_host) return HK_ERR_ARG;
+    if (nx < 1 || ny < 1 || nz < 1 || sizes_cap < 0 || (sizes_cap > 0 && !sizes_host)) return HK_ERR_ARG;
+    const int64_t N = (int64_t)nx * ny * nz;
+    if (N >= MAX_SITES) return HK_ERR_TOO_LARGE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return fail_cuda(ctx, e);
+    const size_t o_phi = 0, o_lab = align256(4 * N), o_hist = o_lab + align256(4 * N);
+    const size_t o_ncl = o_hist + 256, o_sizes = o_ncl + 256;
+    const size_t need = o_sizes + align256(8 * (size_t)std::max<int64_t>(sizes_cap, 1));
+    if (need > ctx->io_bytes) {
+        if (ctx->io) { cudaDeviceSynchronize(); cudaFree(ctx->io); ctx->io = nullptr; ctx->io_bytes = 0; }
+        if (cudaMalloc(&ctx->io, need) != cudaSuccess) { cudaGetLastError(); return HK_ERR_NOMEM; }
+        ctx->io_bytes = need;
+    }
+    char *io = static_cast<char *>(ctx->io);
+    float *phi_d = reinterpret_cast<float *>(io + o_phi);
+    int32_t *lab_d = reinterpret_cast<int32_t *>(io + o_lab);
+    int64_t *hist_d = reinterpret_cast<int64_t *>(io + o_hist);
+    int64_t *ncl_d = reinterpret_cast<int64_t *>(io + o_ncl);
+    int64_t *sizes_d = reinterpret_cast<int64_t *>(io + o_sizes);
+    e = cudaMemcpyAsync(phi_d, phi_host, 4 * N, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return fail_cuda(ctx, e);
+    hk_lattice l;
+    l.phi = phi_d;
+    l.nx = nx; l.ny = ny; l.nz = nz;
+    for (int a = 0; a < 3; ++a) l.periodic[a] = periodic[a];
+    l.labels = lab_d;
+    l.sizes = sizes_d;
+    l.sizes_cap = sizes_cap;
+    l.hist = hist_d;
+    l.n_clusters = ncl_d;
+    int rc = run_lattices(ctx, &l, 1, st);
+    if (rc != HK_OK && rc != HK_ERR_CAPACITY) return rc;
+    int64_t ncl = 0;
+    e = cudaMemcpyAsync(&ncl, ncl_d, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(labels_host, lab_d, 4 * N, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && hist_host) e = cudaMemcpyAsync(hist_host, hist_d, 256, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail_cuda(ctx, e);
+    const int64_t ns = std::min(ncl, sizes_cap);
+    if (ns > 0) {
+        e = cudaMemcpyAsync(sizes_host, sizes_d, 8 * ns, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return fail_cuda(ctx, e);
+    }
+    if (n_clusters_host) *n_clusters_host = ncl;
+    return ncl > sizes_cap ? HK_ERR_CAPACITY : HK_OK;
+}
+
+int hk_set_tile(hk_ctx *ctx, int ty, int tz) {
+    if (!ctx) return HK_ERR_ARG;
+    if (ty == 0 && tz == 0) { ctx->ty = DEFAULT_TY; ctx->tz = DEFAULT_TZ; return HK_OK; }
+    TileInfo ti;
+    if (!hk::tile_info(ty, tz, ti)) return HK_ERR_ARG;
+    ctx->ty = ty;
+    ctx->tz = tz;
+    return HK_OK;
+}
+
+int hk_set_timing(hk_ctx *ctx, int enable) {
+    if (!ctx) return HK_ERR_ARG;
+    if (enable && !ctx->ev[0][0]) {
+        if (cudaSetDevice(ctx->device) != cudaSuccess) return fail_cuda(ctx, cudaGetLastError());
+        for (auto &set : ctx->ev)
+            for (auto &e : set) {
+                const cudaError_t ce = cudaEventCreate(&e);
+                if (ce != cudaSuccess) return fail_cuda(ctx, ce);
+            }
+    }
+    ctx->timing = enable != 0;
+    ctx->ncalls = 0;
+    ctx->nacc = 0;
+    for (auto &a : ctx->acc) a = 0.0;
+    return HK_OK;
+}
+
+int hk_get_timing(hk_ctx *ctx, float *ms_out, int max_n, int *n_out) {
+    if (!ctx || !ms_out || ctx->ncalls == 0) return HK_ERR_ARG;
+    while (ctx->nacc < ctx->ncalls) {
+        const cudaError_t e = fold_slot(ctx, (int)(ctx->nacc % hk_ctx::RING));
+        if (e != cudaSuccess) return fail_cuda(ctx, e);
+    }
+    const int n = std::min(max_n, hk::NUM_PASSES);
+    for (int i = 0; i < n; ++i) ms_out[i] = (float)(ctx->acc[i] / (double)ctx->nacc);
+    if (n_out) *n_out = hk::NUM_PASSES;
+    return HK_OK;
+}
+
+int hk_sync_status(hk_ctx *ctx, void *stream) {
+    if (!ctx) return HK_ERR_ARG;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail_cuda(ctx, e);
+    if (!ctx->dstatus) return HK_OK;
+    int32_t s = 0;
+    e = cudaMemcpy(&s, ctx->dstatus, sizeof(s), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(ctx->dstatus, 0, sizeof(s));
+    if (e != cudaSuccess) return fail_cuda(ctx, e);
+    return s ? HK_ERR_TIMEOUT : HK_OK;
+}
+
+int hk_last_cuda_error(const hk_ctx *ctx) { return ctx ? ctx->last_cuda : 0; }
+
+const char *hk_strerror(int status) {
+    switch (status) {
+        case HK_OK: return "ok";
+        case HK_ERR_ARG: return "invalid argument";
+        case HK_ERR_TOO_LARGE: return "lattice too large (nx*ny*nz >= 2^31)";
+        case HK_ERR_CAPACITY: return "more clusters than sizes_cap";
+        case HK_ERR_CUDA: return "CUDA runtime error";
+        case HK_ERR_TIMEOUT: return "device-side wait timed out";
+        case HK_ERR_NOMEM: return "workspace allocation failed";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,36 @@
+// hk_launch.h -- internal interface between the C ABI (hk_api.cu) and the
+// kernels (hk_kernels.cu).  Not installed; the public interface is include/hk.h.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hk {
+
+struct LatDev;
+struct Work;
+
+constexpr int MAX_LAT_PER_LAUNCH = 128;
+
+struct TileInfo {
+    int ty, tz;
+    int rows;            // tile rows (ty * tz), one 32-bit occupancy word each
+    int face_stride;     // uint16 face entries per tile
+    int max_boundary;    // bound on boundary pieces per tile
+    size_t smem;         // dynamic shared memory of the tile kernels
+};
+
+struct Plan {
+    int64_t ntiles;      // tiles of all lattices in the launch
+    int64_t nseg;        // row segments of all lattices
+    int64_t piece_cap;   // ntiles * max_boundary
+};
+
+bool tile_info(int ty, int tz, TileInfo &ti);
+constexpr int NUM_PASSES = 6;   // tile_label, face_merge, piece_finalize, scan, lattice_finish, flatten
+
+// ev: NUM_PASSES + 1 events recorded around the passes, or nullptr
+cudaError_t launch_label(int ty, int tz, const LatDev *lats, int n, const Plan &P, const Work &W, cudaStream_t st,
+                         cudaEvent_t *ev);
+
+}  // namespace hk

@@ -1,0 +1,276 @@
+"""Thin Python binding of libhk (include/hk.h, include/hk_gen.h).
+
+Argument marshalling only: every step of the labelling runs in the CUDA
+library.  The functions named ``hk_*`` mirror the C entry points one to one
+and take raw pointers (ints) and a stream handle; ``Labeller`` wraps a context
+and accepts torch CUDA tensors.  There is no CPU fallback: if the library
+cannot be loaded or built, importing the symbols raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+HK_OK, HK_ERR_ARG, HK_ERR_TOO_LARGE, HK_ERR_CAPACITY = 0, 1, 2, 3
+HK_ERR_CUDA, HK_ERR_TIMEOUT, HK_ERR_NOMEM = 4, 5, 6
+
+EXPORTED = ("hk_create", "hk_destroy", "hk_workspace_bytes", "hk_reserve", "hk_label", "hk_label_batched",
+            "hk_label_host", "hk_set_tile", "hk_set_timing", "hk_get_timing", "hk_sync_status", "hk_last_cuda_error", "hk_strerror",
+            "hk_gen_iid", "hk_gen_spheres", "hk_gen_capsule")
+
+_lock = threading.Lock()
+_lib = None
+
+
+class HKError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {hk_strerror(status)} (status {status})" if where else hk_strerror(status))
+
+
+class hk_lattice(ctypes.Structure):
+    _fields_ = [("phi", ctypes.c_void_p), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("periodic", ctypes.c_int * 3), ("labels", ctypes.c_void_p), ("sizes", ctypes.c_void_p),
+                ("sizes_cap", ctypes.c_int64), ("hist", ctypes.c_void_p), ("n_clusters", ctypes.c_void_p)]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libhk.so, building it first if it is missing or older than its sources."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if _build.needs_build():
+            _build.build()
+        lib = ctypes.CDLL(_build.LIB)
+        P, I, I64, SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+        sig = {
+            "hk_create": (I, [ctypes.POINTER(P), I]),
+            "hk_destroy": (None, [P]),
+            "hk_workspace_bytes": (SZ, [I, I, I]),
+            "hk_reserve": (I, [P, SZ]),
+            "hk_label": (I, [P, P, I, I, I, P, P, P, I64, P, P, P]),
+            "hk_label_batched": (I, [P, ctypes.POINTER(hk_lattice), I, P]),
+            "hk_label_host": (I, [P, P, I, I, I, P, P, P, I64, P, P, P]),
+            "hk_set_tile": (I, [P, I, I]),
+            "hk_set_timing": (I, [P, I]),
+            "hk_get_timing": (I, [P, ctypes.POINTER(ctypes.c_float), I, ctypes.POINTER(ctypes.c_int)]),
+            "hk_sync_status": (I, [P, P]),
+            "hk_last_cuda_error": (I, [P]),
+            "hk_strerror": (ctypes.c_char_p, [I]),
+            "hk_gen_iid": (I, [P, I, I, I, ctypes.c_uint64, ctypes.c_double, P]),
+            "hk_gen_spheres": (I, [P, I, I, I, P, P, I, ctypes.c_double, P]),
+            "hk_gen_capsule": (I, [P, I, ctypes.c_double, ctypes.c_double, ctypes.c_double, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+# ---- one-to-one wrappers -------------------------------------------------------------------
+
+def hk_create(device: int = 0) -> int:
+    h = ctypes.c_void_p()
+    rc = load().hk_create(ctypes.byref(h), int(device))
+    if rc != HK_OK:
+        raise HKError(rc, "hk_create")
+    return h.value
+
+
+def hk_destroy(ctx: int) -> None:
+    load().hk_destroy(ctx)
+
+
+def hk_workspace_bytes(nx: int, ny: int, nz: int) -> int:
+    return int(load().hk_workspace_bytes(nx, ny, nz))
+
+
+def hk_reserve(ctx: int, nbytes: int) -> int:
+    return load().hk_reserve(ctx, int(nbytes))
+
+
+def _per(periodic):
+    return (ctypes.c_int * 3)(*[int(bool(p)) for p in periodic])
+
+
+def hk_label(ctx, phi, nx, ny, nz, periodic, labels_out, sizes_out, sizes_cap, hist_out, n_clusters_out,
+             stream=0) -> int:
+    return load().hk_label(ctx, phi, nx, ny, nz, _per(periodic), labels_out, sizes_out, int(sizes_cap),
+                           hist_out, n_clusters_out, stream)
+
+
+def hk_label_batched(ctx, lats, stream=0) -> int:
+    arr = (hk_lattice * len(lats))(*lats)
+    return load().hk_label_batched(ctx, arr, len(lats), stream)
+
+
+def hk_label_host(ctx, phi_host, nx, ny, nz, periodic, labels_host, sizes_host, sizes_cap, hist_host,
+                  n_clusters_host, stream=0) -> int:
+    return load().hk_label_host(ctx, phi_host, nx, ny, nz, _per(periodic), labels_host, sizes_host,
+                                int(sizes_cap), hist_host, n_clusters_host, stream)
+
+
+def hk_set_tile(ctx, ty, tz) -> int:
+    return load().hk_set_tile(ctx, ty, tz)
+
+
+PASS_NAMES = ("tile_label", "face_merge", "piece_finalize", "scan", "lattice_finish", "flatten")
+
+
+def hk_set_timing(ctx, enable: bool) -> int:
+    return load().hk_set_timing(ctx, int(bool(enable)))
+
+
+def hk_get_timing(ctx):
+    """Per-pass milliseconds of the context's last timed call (synchronises on it)."""
+    buf = (ctypes.c_float * 16)()
+    n = ctypes.c_int(0)
+    rc = load().hk_get_timing(ctx, buf, 16, ctypes.byref(n))
+    if rc != HK_OK:
+        raise HKError(rc, "hk_get_timing")
+    return [float(buf[i]) for i in range(n.value)]
+
+
+def hk_sync_status(ctx, stream=0) -> int:
+    return load().hk_sync_status(ctx, stream)
+
+
+def hk_last_cuda_error(ctx) -> int:
+    return load().hk_last_cuda_error(ctx)
+
+
+def hk_strerror(status: int) -> str:
+    return load().hk_strerror(int(status)).decode()
+
+
+def hk_gen_iid(phi, nx, ny, nz, seed, occupancy, stream=0) -> int:
+    return load().hk_gen_iid(phi, nx, ny, nz, int(seed), float(occupancy), stream)
+
+
+def hk_gen_spheres(phi, nx, ny, nz, centres, radii, reach=8.0, stream=0) -> int:
+    c = np.ascontiguousarray(centres, dtype=np.float64).reshape(-1)
+    r = np.ascontiguousarray(radii, dtype=np.float64).reshape(-1)
+    return load().hk_gen_spheres(phi, nx, ny, nz, c.ctypes.data, r.ctypes.data, int(r.size), float(reach), stream)
+
+
+def hk_gen_capsule(phi, L, ax, ay, az, stream=0) -> int:
+    return load().hk_gen_capsule(phi, int(L), float(ax), float(ay), float(az), stream)
+
+
+# ---- torch convenience ---------------------------------------------------------------------
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Labeller:
+    """A libhk context bound to one CUDA device, taking torch tensors.
+
+    ``label(phi)`` with ``phi`` a float32 CUDA tensor of shape (nz, ny, nx)
+    returns ``(labels, sizes, hist, n_clusters)`` as CUDA tensors (sizes has
+    ``sizes_cap`` entries, default ceil(N/2); the first n_clusters are valid).
+    """
+
+    def __init__(self, device: int = 0, tile: tuple | None = None):
+        self.device = int(device)
+        self.ctx = hk_create(self.device)
+        self.tile = (16, 16)
+        if tile is not None:
+            self.set_tile(*tile)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            hk_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_tile(self, ty: int, tz: int):
+        rc = hk_set_tile(self.ctx, ty, tz)
+        if rc != HK_OK:
+            raise HKError(rc, "hk_set_tile")
+        self.tile = (ty, tz)
+
+    def sync_status(self, stream=None):
+        """Synchronise and raise if a bounded device-side loop gave up since the last check."""
+        rc = hk_sync_status(self.ctx, _stream_handle(stream))
+        if rc != HK_OK:
+            raise HKError(rc, "hk_sync_status")
+
+    def reserve(self, nbytes: int):
+        rc = hk_reserve(self.ctx, nbytes)
+        if rc != HK_OK:
+            raise HKError(rc, "hk_reserve")
+
+    @staticmethod
+    def alloc_outputs(shape, device, sizes_cap=None):
+        import torch
+        n = int(np.prod(shape))
+        cap = (n + 1) // 2 if sizes_cap is None else int(sizes_cap)
+        labels = torch.empty(shape, dtype=torch.int32, device=device)
+        sizes = torch.empty(max(cap, 1), dtype=torch.int64, device=device)
+        hist = torch.empty(32, dtype=torch.int64, device=device)
+        ncl = torch.empty(1, dtype=torch.int64, device=device)
+        return labels, sizes, hist, ncl, cap
+
+    def label(self, phi, periodic=(1, 1, 1), out=None, sizes_cap=None, stream=None, check=True):
+        import torch
+        if not (phi.is_cuda and phi.dtype == torch.float32 and phi.dim() == 3 and phi.is_contiguous()):
+            raise ValueError("phi must be a contiguous float32 CUDA tensor of shape (nz, ny, nx)")
+        nz, ny, nx = phi.shape
+        if out is None:
+            out = self.alloc_outputs(phi.shape, phi.device, sizes_cap)
+        labels, sizes, hist, ncl, cap = out
+        rc = hk_label(self.ctx, phi.data_ptr(), nx, ny, nz, periodic, labels.data_ptr(), sizes.data_ptr(), cap,
+                      hist.data_ptr(), ncl.data_ptr(), _stream_handle(stream))
+        if check and rc != HK_OK:
+            raise HKError(rc, "hk_label")
+        return labels, sizes, hist, ncl
+
+    def label_batched(self, items, stream=None, check=True):
+        """items: list of (phi, periodic, (labels, sizes, hist, ncl, cap)) with CUDA tensors."""
+        lats = []
+        for phi, periodic, (labels, sizes, hist, ncl, cap) in items:
+            nz, ny, nx = phi.shape
+            lats.append(hk_lattice(phi.data_ptr(), nx, ny, nz, (ctypes.c_int * 3)(*[int(bool(p)) for p in periodic]),
+                                   labels.data_ptr(), sizes.data_ptr(), int(cap), hist.data_ptr(), ncl.data_ptr()))
+        rc = hk_label_batched(self.ctx, lats, _stream_handle(stream))
+        if check and rc != HK_OK:
+            raise HKError(rc, "hk_label_batched")
+        return rc
+
+    def label_host(self, phi: np.ndarray, periodic=(1, 1, 1), sizes_cap=None, out=None, stream=None):
+        """Host buffers in and out (numpy); copies run inside the call."""
+        phi = np.ascontiguousarray(phi, dtype=np.float32)
+        nz, ny, nx = phi.shape
+        n = phi.size
+        cap = (n + 1) // 2 if sizes_cap is None else int(sizes_cap)
+        if out is None:
+            out = (np.empty(phi.shape, np.int32), np.empty(max(cap, 1), np.int64), np.empty(32, np.int64),
+                   np.empty(1, np.int64))
+        labels, sizes, hist, ncl = out
+        rc = hk_label_host(self.ctx, phi.ctypes.data, nx, ny, nz, periodic, labels.ctypes.data,
+                           sizes.ctypes.data, cap, hist.ctypes.data, ncl.ctypes.data, _stream_handle(stream))
+        if rc not in (HK_OK, HK_ERR_CAPACITY):
+            raise HKError(rc, "hk_label_host")
+        k = int(ncl[0])
+        return labels, sizes[:min(k, cap)], hist, k
