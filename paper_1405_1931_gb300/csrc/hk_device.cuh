@@ -158,6 +158,19 @@ __device__ __forceinline__ int s_find(int *par, int x, int cap, int32_t *status)
     return x;
 }
 
+// Read-only find for the compression step: without halving stores, no thread
+// can overwrite another thread's final par[i] = root with an older ancestor.
+__device__ __forceinline__ int s_find_ro(const int *par, int x, int cap, int32_t *status) {
+    const volatile int *vp = par;
+    int p = vp[x];
+    for (int it = 0; p != x; ++it) {
+        if (it > cap) { atomicOr(status, STATUS_LOCAL_LOOP); return x; }
+        x = p;
+        p = vp[x];
+    }
+    return x;
+}
+
 // Each retry strictly lowers b, so at most `cap` rounds.
 __device__ __forceinline__ void s_union(int *par, int a, int b, int cap, int32_t *status) {
     for (int it = 0; it <= cap; ++it) {
@@ -252,7 +265,7 @@ __device__ void tile_local_label(TileSmem<TY, TZ> &S, const TileGeo &g, int32_t 
     __syncthreads();
 
     // 3. full compression
-    for (int i = r; i < total; i += SH::NT) S.par[i] = s_find(S.par, i, total, status);
+    for (int i = r; i < total; i += SH::NT) S.par[i] = s_find_ro(S.par, i, total, status);
     __syncthreads();
 
     // 4. piece sizes and boundary flags
@@ -311,6 +324,19 @@ __device__ __forceinline__ int g_find(int32_t *parent, int x, int64_t cap, int32
         if (gp == p) return p;
         __stcg(parent + x, gp);    // path halving
         x = gp;
+        p = __ldcg(parent + x);
+    }
+    return x;
+}
+
+// Read-only find for the compression pass: no halving writes, so the one store
+// each thread makes afterwards (parent[pid] = root) cannot be overwritten by
+// another thread's halving store of an older, non-root ancestor.
+__device__ __forceinline__ int g_find_ro(const int32_t *parent, int x, int64_t cap, int32_t *status) {
+    int p = __ldcg(parent + x);
+    for (int64_t it = 0; p != x; ++it) {
+        if (it > cap) { atomicOr(status, STATUS_GLOBAL_LOOP); return x; }
+        x = p;
         p = __ldcg(parent + x);
     }
     return x;

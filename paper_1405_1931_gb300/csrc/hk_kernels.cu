@@ -197,7 +197,7 @@ k_piece_finalize(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles)
     const LatDev &L = B.lat[lat];
     for (int j = lane; j < ti.y; j += 32) {
         const int pid = ti.x + j;
-        const int root = g_find(W.parent, pid, W.piece_cap, W.status);
+        const int root = g_find_ro(W.parent, pid, W.piece_cap, W.status);
         if (root != pid) {
             __stcg(W.parent + pid, root);
             atomicAdd(W.psize + root, W.psize[pid]);
