@@ -5,6 +5,8 @@
 #include <cstring>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include "../../include/hk.h"
@@ -42,7 +44,7 @@ constexpr int64_t MAX_SITES = (int64_t)1 << 31;
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t mask, cnt, pre, bsum, face, tinfo, parent, key, psize, npieces, status, ncl, total;
+    size_t mask, codes, cnt, pre, bsum, face, tinfo, parent, key, psize, ncl, total;
 };
 
 Layout make_layout(const TileInfo &ti, const Plan &P) {
@@ -51,16 +53,15 @@ Layout make_layout(const TileInfo &ti, const Plan &P) {
     auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
     const int64_t nb = (P.nseg + 4096) / 4096;
     L.mask = take((size_t)P.ntiles * ti.rows * 4);
+    L.codes = take((size_t)P.ntiles * ti.maxruns * 2);
     L.cnt = take((size_t)P.nseg * 4);
     L.pre = take((size_t)(P.nseg + 1) * 4);
     L.bsum = take((size_t)nb * 4);
     L.face = take((size_t)P.ntiles * ti.face_stride * 2);
-    L.tinfo = take((size_t)P.ntiles * 8);
+    L.tinfo = take((size_t)P.ntiles * 16);
     L.parent = take((size_t)P.piece_cap * 4);
     L.key = take((size_t)P.piece_cap * 4);
     L.psize = take((size_t)P.piece_cap * 4);
-    L.npieces = take(4);
-    L.status = take(4);
     L.ncl = take((size_t)hk::MAX_LAT_PER_LAUNCH * 8);
     L.total = off;
     return L;
@@ -112,6 +113,49 @@ int check_lattice(const hk_lattice &l) {
     return HK_OK;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// Tensor maps for TMA tile loads of phi and tile stores of labels: box (32, ty, tz),
+// zero fill outside the lattice.  TMA needs 16-byte aligned base addresses and row
+// pitches, so nx must be a multiple of 4; otherwise tm.valid stays 0 and the
+// kernels use cp.async loads and plain stores.
+void make_tmaps(const hk_lattice &l, int ty, int tz, hk::TmapPair &tm) {
+    std::memset(&tm, 0, sizeof(tm));
+    auto fn = encode_fn();
+    if (!fn || (l.nx % 4) != 0 || (reinterpret_cast<uintptr_t>(l.phi) & 15) ||
+        (reinterpret_cast<uintptr_t>(l.labels) & 15))
+        return;
+    const cuuint64_t dims[3] = {(cuuint64_t)l.nx, (cuuint64_t)l.ny, (cuuint64_t)l.nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)l.nx * 4, (cuuint64_t)l.nx * l.ny * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)hk::TX, (cuuint32_t)ty, (cuuint32_t)tz};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (fn(&tm.phi, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(l.phi), dims, strides, box, estr,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return;
+    if (fn(&tm.labels, CU_TENSOR_MAP_DATA_TYPE_INT32, 3, l.labels, dims, strides, box, estr,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return;
+    tm.valid = 1;
+}
+
 // Add the pass durations of ring slot `slot` (a completed call) to the totals.
 cudaError_t fold_slot(hk_ctx *ctx, int slot) {
     cudaError_t e = cudaEventSynchronize(ctx->ev[slot][hk::NUM_PASSES]);
@@ -142,12 +186,32 @@ int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st) {
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return fail_cuda(ctx, e);
 
+    // Launch chunks: at most MAX_LAT_PER_LAUNCH lattices, and few enough tiles that
+    // every piece id (tile * max_boundary + k) and every root count fits in 31 bits.
+    const int64_t max_tiles = ((int64_t)1 << 31) / ti.max_boundary - 1;
+    std::vector<int> chunk_start;
+    {
+        int c0 = 0;
+        while (c0 < n) {
+            chunk_start.push_back(c0);
+            Plan P{0, 0, 0};
+            int c1 = c0;
+            while (c1 < n && c1 - c0 < hk::MAX_LAT_PER_LAUNCH) {
+                Plan Q = P;
+                add_lattice(ti, lats[c1].nx, lats[c1].ny, lats[c1].nz, Q);
+                if (c1 > c0 && Q.ntiles > max_tiles) break;
+                P = Q;
+                ++c1;
+            }
+            c0 = c1;
+        }
+        chunk_start.push_back(n);
+    }
     // size the workspace for the largest chunk
     size_t need = 0;
-    for (int c0 = 0; c0 < n; c0 += hk::MAX_LAT_PER_LAUNCH) {
+    for (size_t c = 0; c + 1 < chunk_start.size(); ++c) {
         Plan P{0, 0, 0};
-        for (int i = c0; i < std::min(n, c0 + hk::MAX_LAT_PER_LAUNCH); ++i)
-            add_lattice(ti, lats[i].nx, lats[i].ny, lats[i].nz, P);
+        for (int i = chunk_start[c]; i < chunk_start[c + 1]; ++i) add_lattice(ti, lats[i].nx, lats[i].ny, lats[i].nz, P);
         P.piece_cap = P.ntiles * ti.max_boundary;
         need = std::max(need, make_layout(ti, P).total);
     }
@@ -162,8 +226,9 @@ int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st) {
 
     bool any_check = false;
     std::vector<int64_t> counts(n, 0);
-    for (int c0 = 0; c0 < n; c0 += hk::MAX_LAT_PER_LAUNCH) {
-        const int cn = std::min(n - c0, hk::MAX_LAT_PER_LAUNCH);
+    for (size_t c = 0; c + 1 < chunk_start.size(); ++c) {
+        const int c0 = chunk_start[c];
+        const int cn = chunk_start[c + 1] - c0;
         Plan P{0, 0, 0};
         std::vector<LatDev> dev(cn);
         for (int i = 0; i < cn; ++i) {
@@ -190,15 +255,15 @@ int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st) {
         char *base = static_cast<char *>(ctx->ws);
         Work W;
         W.mask = reinterpret_cast<uint32_t *>(base + Ly.mask);
+        W.codes = reinterpret_cast<uint16_t *>(base + Ly.codes);
         W.cnt = reinterpret_cast<uint32_t *>(base + Ly.cnt);
         W.pre = reinterpret_cast<uint32_t *>(base + Ly.pre);
         W.bsum = reinterpret_cast<uint32_t *>(base + Ly.bsum);
         W.face = reinterpret_cast<uint16_t *>(base + Ly.face);
-        W.tinfo = reinterpret_cast<int2 *>(base + Ly.tinfo);
+        W.tinfo = reinterpret_cast<int4 *>(base + Ly.tinfo);
         W.parent = reinterpret_cast<int32_t *>(base + Ly.parent);
         W.key = reinterpret_cast<int32_t *>(base + Ly.key);
         W.psize = reinterpret_cast<int32_t *>(base + Ly.psize);
-        W.npieces = reinterpret_cast<int32_t *>(base + Ly.npieces);
         W.status = ctx->dstatus;
         W.piece_cap = P.piece_cap;
         int64_t *slots = reinterpret_cast<int64_t *>(base + Ly.ncl);
@@ -216,7 +281,10 @@ int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st) {
             ev = ctx->ev[slot];
             ctx->ncalls += 1;
         }
-        e = hk::launch_label(ctx->ty, ctx->tz, dev.data(), cn, P, W, st, ev);
+        hk::TmapPair tm;
+        if (cn == 1) make_tmaps(lats[c0], ctx->ty, ctx->tz, tm);
+        else std::memset(&tm, 0, sizeof(tm));
+        e = hk::launch_label(ctx->ty, ctx->tz, dev.data(), cn, P, W, tm, st, ev);
         if (e != cudaSuccess) return fail_cuda(ctx, e);
         if (chunk_check) {
             // the capacity rule needs the counts: wait for this chunk

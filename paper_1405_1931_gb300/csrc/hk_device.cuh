@@ -1,5 +1,5 @@
-// hk_device.cuh -- device-side data structures and the tile-local labelling
-// shared by the tile pass (K1) and the flatten pass (K4).
+// hk_device.cuh -- device-side data structures, PTX helpers (TMA, mbarrier,
+// cp.async) and the union-find primitives of the labelling passes.
 //
 // Tiles are 32 sites along x (one 32-bit occupancy word per tile row) by TY
 // rows along y by TZ planes along z.  Inside a tile the Hoshen-Kopelman raster
@@ -12,12 +12,21 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace hk {
 
 constexpr int TX = 32;
 constexpr uint16_t FACE_NONE = 0xFFFF;
+// Run codes (one uint16 per x-run, written by the tile pass, decoded by flatten):
+//   CODE_BOUNDARY | k               a run of boundary piece k of the tile
+//   CODE_BOUNDARY | CODE_ROOT | k   the first run of boundary piece k
+//   CODE_ROOT | size                the first run of an interior piece (its size, <= 8192)
+//   r (< CODE_ROOT)                 another run of the interior piece whose first run is r
+constexpr uint16_t CODE_BOUNDARY = 0x8000;
+constexpr uint16_t CODE_ROOT = 0x4000;
+constexpr uint16_t CODE_LOW = 0x3fff;
 
 // One lattice of a launch.  Every pass works on the concatenated tiles of all
 // lattices; tile0/seg0 locate this lattice's slice of the global tile and
@@ -40,30 +49,44 @@ struct LatDev {
 // Workspace pointers shared by all passes of one launch.
 struct Work {
     uint32_t *mask;     // [ntiles * R] occupancy words, tile-major (tile t, row r)
+    uint16_t *codes;    // [ntiles * MAXRUNS] one code per run (CODE_* above)
     uint32_t *cnt;      // [nseg] cluster roots per segment (row-major segment order)
     uint32_t *pre;      // [nseg + 1] exclusive prefix of cnt
     uint32_t *bsum;     // [nblocks] scan block sums
     uint16_t *face;     // [ntiles * face_stride] boundary-piece numbers of face sites
-    int2 *tinfo;        // [ntiles] (piece base, piece count) of each tile
-    int32_t *parent;    // [piece_cap] union-find parent over boundary pieces
-    int32_t *key;       // [piece_cap] lattice-local site index of the piece's first site
-    int32_t *psize;     // [piece_cap] piece size, then cluster size at cluster roots
-    int32_t *npieces;   // [1] piece allocation counter
+    int4 *tinfo;        // [ntiles] (piece base, piece count, run count, 0) of each tile
+    int32_t *parent;    // [piece_cap] union-find parent over boundary pieces; tile t owns
+                        // the slice [t * MAX_BOUNDARY, t * MAX_BOUNDARY + piece count)
+    int32_t *key;       // [piece_cap] lattice-local site index of the piece's first site;
+                        // after piece_finalize: the label of the piece's cluster
+    int32_t *psize;     // [piece_cap] piece size; after piece_finalize: the cluster size at
+                        // the cluster's root piece, -1 elsewhere
     int32_t *status;    // [1] device-side error flags (STATUS_*), owned by the context
     int64_t piece_cap;  // entries of parent/key/psize: bounds every union-find path
 };
 
+// Tensor maps of the single-lattice fast path (TMA tile loads of phi and TMA
+// tile stores of labels).  Unused when `valid` is 0.
+struct TmapPair {
+    CUtensorMap phi;
+    CUtensorMap labels;
+    int valid;
+};
+
 // A union-find path longer than the number of its nodes means corrupted
-// parents; every loop below is capped by that count, and on reaching the cap
-// it records one of these flags and stops instead of spinning.
+// parents, and a TMA wait that never completes means a lost copy; every loop
+// below is capped, and on reaching the cap it records one of these flags and
+// stops instead of spinning.
 constexpr int32_t STATUS_LOCAL_LOOP = 1;
 constexpr int32_t STATUS_GLOBAL_LOOP = 2;
+constexpr int32_t STATUS_TMA_TIMEOUT = 4;
 
 template <int TY, int TZ>
 struct TileShape {
     static constexpr int R = TY * TZ;            // rows per tile
+    static constexpr int SITES = TX * R;
     static constexpr int MAXRUNS = 16 * R;       // at most 16 runs in a 32-site row
-    static constexpr int NT = R;                 // one thread per row
+    static constexpr int NT = R;                 // threads per CTA: one per row
     // face layout inside a tile's face block
     static constexpr int OFF_LX = 0;
     static constexpr int OFF_HX = R;
@@ -78,25 +101,8 @@ struct TileShape {
     static constexpr int MAX_BOUNDARY = (R + 1) / 2 * 2 + (TX * TZ + 1) / 2 * 2 + (TX * TY + 1) / 2 * 2;
 };
 
-template <int TY, int TZ>
-struct TileSmem {
-    using S = TileShape<TY, TZ>;
-    uint32_t m[S::R];           // occupancy word of each row
-    int rbase[S::R];            // first run id of each row
-    int par[S::MAXRUNS];        // union-find over run ids (par[i] <= i)
-    int aux[S::MAXRUNS];        // per root: piece size, later the final label
-    int kmap[S::MAXRUNS];       // per boundary root: boundary number inside the tile
-    uint32_t bflag[S::MAXRUNS / 32];   // boundary flag per run id (meaningful at roots)
-    int warp_tmp[32];
-    int nruns;
-    int nbound;
-    int base;
-    int hist[32];
-};
-
 // Tile geometry of global tile t.
 struct TileGeo {
-    int lat;
     int bx, by, bz;
     int x0, y0, z0;
     int lastX, lastY, lastZ;    // last valid local coordinate (ragged edges)
@@ -114,9 +120,8 @@ __device__ __forceinline__ int find_lattice(const LatDev *lats, int nlat, int64_
 }
 
 template <int TY, int TZ>
-__device__ __forceinline__ TileGeo tile_geo(const LatDev &L, int lat, int64_t t) {
+__device__ __forceinline__ TileGeo tile_geo(const LatDev &L, int64_t t) {
     TileGeo g;
-    g.lat = lat;
     int64_t lt = t - L.tile0;
     g.bx = (int)(lt % L.nbx);
     int64_t q = lt / L.nbx;
@@ -139,8 +144,68 @@ __device__ __forceinline__ TileGeo tile_geo(const LatDev &L, int lat, int64_t t)
 __device__ __forceinline__ uint32_t run_starts(uint32_t m) { return m & ~(m << 1); }
 // bits 0..x set
 __device__ __forceinline__ uint32_t le_mask(int x) { return (2u << x) - 1u; }
-// run id (global within the tile) of occupied site x of a row with run starts rs
+// run id (within the tile) of occupied site x of a row with run starts rs
 __device__ __forceinline__ int run_of(int rbase, uint32_t rs, int x) { return rbase + __popc(rs & le_mask(x)) - 1; }
+// length of the run starting at bit x0 of m
+__device__ __forceinline__ int run_len(uint32_t m, int x0) {
+    const uint32_t v = m >> x0;
+    return (v == 0xffffffffu) ? 32 : __ffs(~v) - 1;
+}
+
+// ---- PTX helpers ----------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// TMA tile load of box (32, TY, TZ) at element coordinates (x, y, z); x*4 bytes is a multiple of 16.
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+// TMA tile store; elements outside the tensor are not written.  Coordinates are never negative.
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, const void *src, int x, int y, int z) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];"
+                 ::"l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(src))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// 4-byte asynchronous global->shared copy; src_bytes == 0 writes a zero.
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Wait for phase `parity` of an mbarrier with an iteration cap; returns false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    for (uint32_t it = 0; it < (1u << 26); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
 
 // ---- shared-memory union-find over run ids (union by minimum id) ----------------------
 // par[i] <= i always holds, so a path visits at most `cap` (= number of runs) ids.
@@ -171,7 +236,7 @@ __device__ __forceinline__ int s_find_ro(const int *par, int x, int cap, int32_t
     return x;
 }
 
-// Each retry strictly lowers b, so at most `cap` rounds.
+// Each retry strictly lowers max(a, b), so at most `cap` rounds.
 __device__ __forceinline__ void s_union(int *par, int a, int b, int cap, int32_t *status) {
     for (int it = 0; it <= cap; ++it) {
         a = s_find(par, a, cap, status);
@@ -185,13 +250,13 @@ __device__ __forceinline__ void s_union(int *par, int a, int b, int cap, int32_t
     atomicOr(status, STATUS_LOCAL_LOOP);
 }
 
-// join the runs of row r and row q that overlap along x
-__device__ __forceinline__ void join_rows(int *par, uint32_t m, uint32_t rs, int rb, uint32_t mq, int rbq, int cap,
+// join the runs of row r and row q that overlap along x (used for the rare in-tile wraps)
+__device__ __forceinline__ void join_rows(int *par, uint32_t m, int rb, uint32_t mq, int rbq, int cap,
                                           int32_t *status) {
     uint32_t o = m & mq;
     if (!o) return;
+    const uint32_t rs = run_starts(m), rsq = run_starts(mq);
     uint32_t os = run_starts(o);
-    uint32_t rsq = run_starts(mq);
     while (os) {
         int x = __ffs(os) - 1;
         os &= os - 1;
@@ -199,7 +264,7 @@ __device__ __forceinline__ void join_rows(int *par, uint32_t m, uint32_t rs, int
     }
 }
 
-// Block-wide exclusive scan of one int per thread (blockDim.x == NT, NT % 32 == 0).
+// Block-wide exclusive scan of one int per thread (blockDim.x == NT, NT % 32 == 0, NT <= 992).
 template <int NT>
 __device__ __forceinline__ int block_exscan(int v, int *warp_tmp, int &total) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -229,87 +294,6 @@ __device__ __forceinline__ int block_exscan(int v, int *warp_tmp, int &total) {
     return r;
 }
 
-// Tile-local labelling from the occupancy words in S.m (filled by the caller).
-// On return: S.par[i] is the root run of run i, S.aux[root] the piece size,
-// S.bflag marks boundary roots, S.kmap[root] numbers the boundary roots in run
-// order, S.nbound their count.  Identical in K1 and K4, so both derive the same
-// pieces and the same boundary numbering.
-template <int TY, int TZ>
-__device__ void tile_local_label(TileSmem<TY, TZ> &S, const TileGeo &g, int32_t *status) {
-    using SH = TileShape<TY, TZ>;
-    const int r = threadIdx.x;               // one row per thread
-    const int ly = r % TY, lz = r / TY;
-    const uint32_t m = S.m[r];
-    const uint32_t rs = run_starts(m);
-
-    // 1. run ids: exclusive scan of run counts over rows
-    int total;
-    const int rb = block_exscan<SH::NT>(__popc(rs), S.warp_tmp, total);
-    S.rbase[r] = rb;
-    if (r == 0) S.nruns = total;
-    for (int i = r; i < total; i += SH::NT) { S.par[i] = i; S.aux[i] = 0; }
-    for (int i = r; i < (total + 31) / 32; i += SH::NT) S.bflag[i] = 0u;
-    __syncthreads();
-
-    // 2. unions with the y-1 and z-1 rows, and periodic edges inside the tile
-    if (m) {
-        if (ly > 0) join_rows(S.par, m, rs, rb, S.m[r - 1], S.rbase[r - 1], total, status);
-        if (lz > 0) join_rows(S.par, m, rs, rb, S.m[r - TY], S.rbase[r - TY], total, status);
-        if (g.wrapY && ly == g.lastY && ly > 0)
-            join_rows(S.par, m, rs, rb, S.m[r - ly], S.rbase[r - ly], total, status);
-        if (g.wrapZ && lz == g.lastZ && lz > 0)
-            join_rows(S.par, m, rs, rb, S.m[r - lz * TY], S.rbase[r - lz * TY], total, status);
-        if (g.wrapX && g.lastX > 0 && (m & 1u) && ((m >> g.lastX) & 1u))
-            s_union(S.par, rb, run_of(rb, rs, g.lastX), total, status);
-    }
-    __syncthreads();
-
-    // 3. full compression
-    for (int i = r; i < total; i += SH::NT) S.par[i] = s_find_ro(S.par, i, total, status);
-    __syncthreads();
-
-    // 4. piece sizes and boundary flags
-    if (m) {
-        const bool face_row = (ly == 0 && g.extYlo) || (ly == g.lastY && g.extYhi) ||
-                              (lz == 0 && g.extZlo) || (lz == g.lastZ && g.extZhi);
-        uint32_t w = rs;
-        int id = rb;
-        while (w) {
-            const int x0 = __ffs(w) - 1;
-            w &= w - 1;
-            const uint32_t v = m >> x0;                       // bit 0 is site x0
-            const int len = (v == 0xffffffffu) ? 32 : __ffs(~v) - 1;
-            const int root = S.par[id];
-            atomicAdd(&S.aux[root], len);
-            const bool touch = face_row || (x0 == 0 && g.extXlo) ||
-                               (g.extXhi && x0 <= g.lastX && x0 + len - 1 >= g.lastX);
-            if (touch) atomicOr(&S.bflag[root >> 5], 1u << (root & 31));
-            ++id;
-        }
-    }
-    __syncthreads();
-
-    // 5. number the boundary roots in run order
-    constexpr int PER = SH::MAXRUNS / SH::NT;   // 16 run ids per thread
-    const int i0 = r * PER;
-    int cnt = 0;
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        const int i = i0 + j;
-        if (i < total && S.par[i] == i && ((S.bflag[i >> 5] >> (i & 31)) & 1u)) ++cnt;
-    }
-    int nb;
-    int k = block_exscan<SH::NT>(cnt, S.warp_tmp, nb);
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        const int i = i0 + j;
-        if (i < total && S.par[i] == i && ((S.bflag[i >> 5] >> (i & 31)) & 1u)) S.kmap[i] = k++;
-    }
-    if (r == 0) S.nbound = nb;
-    __syncthreads();
-}
-
-__device__ __forceinline__ bool is_boundary(const uint32_t *bflag, int i) { return (bflag[i >> 5] >> (i & 31)) & 1u; }
 
 // ---- global union-find over boundary pieces --------------------------------------------
 // Links go from a root to a root with a smaller key (the piece's first site), so

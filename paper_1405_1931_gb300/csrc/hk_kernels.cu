@@ -1,8 +1,11 @@
 // hk_kernels.cu -- the labelling passes.
 //
-//   K1 tile_label     read phi once, write the occupancy mask, label each tile
-//                     locally (Sec. 2's rules become union-find over x-runs),
-//                     register boundary pieces, write face summaries and the
+//   K1 tile_label     persistent: stream phi tiles into shared memory (TMA
+//                     tensor loads, prefetching the next tile while the
+//                     current one is labelled), write the occupancy mask,
+//                     label each tile locally (Sec. 2's rules become
+//                     union-find over x-runs), register boundary pieces, and
+//                     write one code per run, the face summaries and the
 //                     per-row count of interior cluster roots.
 //   K2 face_merge     join boundary pieces across tile faces and periodic
 //                     edges: the intra-GPU counterpart of Sec. 3's halo
@@ -12,9 +15,9 @@
 //                     roots and count cluster roots per row segment.
 //   S1-S3 scan        exclusive prefix of the root counts: the compactified
 //                     cluster numbering 1..n of Sec. 2 in row-major order.
-//   K4 flatten        rebuild each tile's local labelling from the mask, map
-//                     pieces to their cluster's smallest site index, write the
-//                     labels, the sizes in label order and the histogram.
+//   K4 flatten        persistent: decode the run codes, write the labels
+//                     (staged in shared memory, TMA tensor stores), the sizes
+//                     in label order and the histogram.
 #include "hk_device.cuh"
 #include "hk_launch.h"
 
@@ -30,103 +33,274 @@ struct LatBatch {
 // --------------------------------------------------------------------------------------
 // K1: tile labelling
 // --------------------------------------------------------------------------------------
+template <int TY, int TZ>
+struct LabelSmem {
+    using SH = TileShape<TY, TZ>;
+    alignas(128) float phi[SH::SITES];     // tile of phi, [lz][ly][x] (TMA / cp.async destination)
+    uint32_t m[SH::R];                     // occupancy word of each row
+    int rbase[SH::R];                      // first run id of each row
+    int par[SH::MAXRUNS];                  // union-find over run ids; after numbering a
+                                           // boundary root i holds -1 - (its boundary number)
+    int aux[SH::MAXRUNS];                  // union pair lists, then piece sizes at roots
+    uint8_t bflag[SH::MAXRUNS];            // boundary flag per root (plain stores of 1)
+    int warp_tmp[32];
+    uint64_t mbar;
+};
+
+// Decode of par[] after numbering: boundary number of run i's piece, or -1 if interior.
+__device__ __forceinline__ int piece_k(const int *par, int i) {
+    const int v = par[i];
+    if (v < 0) return -1 - v;            // i is a boundary root
+    const int w = par[v];
+    return w < 0 ? -1 - w : -1;
+}
+
 template <int TY, int TZ, int NL>
 __global__ void __launch_bounds__(TY * TZ)
-k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W) {
+k_tile_label(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapPair tm, Work W, int64_t ntiles) {
     using SH = TileShape<TY, TZ>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TileSmem<TY, TZ> &S = *reinterpret_cast<TileSmem<TY, TZ> *>(smem_raw);
-    constexpr int R = SH::R, NT = SH::NT, NW = NT / 32;
+    constexpr int R = SH::R, NT = SH::NT, NW = NT / 32, MR = SH::MAXRUNS;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    LabelSmem<TY, TZ> &S = *reinterpret_cast<LabelSmem<TY, TZ> *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const bool use_tma = (NL == 1) && tm.valid;
 
-    const int64_t t = blockIdx.x;
-    const int lat = (NL == 1) ? 0 : find_lattice(B.lat, B.n, t);
-    const LatDev &L = B.lat[lat];
-    const TileGeo g = tile_geo<TY, TZ>(L, lat, t);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (tid == 0) {
+        mbar_init(&S.mbar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
 
-    // a1: coalesced 128-byte row loads of phi, occupancy by warp ballot
-    {
-        const int64_t sxy = (int64_t)L.nx * L.ny;
-        const float *base = L.phi + (int64_t)g.z0 * sxy + (int64_t)g.y0 * L.nx + g.x0 + lane;
-        const bool xin = lane <= g.lastX;
-        constexpr int U = 8;
-        for (int r0 = wid; r0 < R; r0 += NW * U) {
-            float v[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int r = r0 + u * NW;
-                const int ly = r % TY, lz = r / TY;
-                v[u] = 0.0f;
-                if (r < R && xin && ly <= g.lastY && lz <= g.lastZ)
-                    v[u] = __ldcs(base + (int64_t)lz * sxy + (int64_t)ly * L.nx);
+    // a1: start the copy of tile t's phi into S.phi (zero fill outside the lattice)
+    auto issue_load = [&](int64_t t) {
+        const LatDev &L = B.lat[(NL == 1) ? 0 : find_lattice(B.lat, B.n, t)];
+        const TileGeo g = tile_geo<TY, TZ>(L, t);
+        if (use_tma) {
+            if (tid == 0) {
+                fence_proxy_async();
+                mbar_arrive_expect_tx(&S.mbar, SH::SITES * 4);
+                tma_load_3d(S.phi, &tm.phi, &S.mbar, g.x0, g.y0, g.z0);
             }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int r = r0 + u * NW;
-                const uint32_t word = __ballot_sync(0xffffffffu, v[u] > 0.0f);
-                if (lane == 0 && r < R) S.m[r] = word;
+        } else {
+            const int64_t sxy = (int64_t)L.nx * L.ny;
+            for (int e = tid; e < SH::SITES; e += NT) {
+                const int x = e & 31, rr = e >> 5, ly = rr % TY, lz = rr / TY;
+                const bool ok = x <= g.lastX && ly <= g.lastY && lz <= g.lastZ;
+                const float *src =
+                    ok ? L.phi + (int64_t)(g.z0 + lz) * sxy + (int64_t)(g.y0 + ly) * L.nx + g.x0 + x : L.phi;
+                cp_async4(&S.phi[e], src, ok ? 4 : 0);
+            }
+            cp_async_commit();
+        }
+    };
+
+    uint32_t phase = 0;
+    int64_t t = blockIdx.x;
+    if (t < ntiles) issue_load(t);
+    for (; t < ntiles; t += gridDim.x) {
+        const LatDev &L = B.lat[(NL == 1) ? 0 : find_lattice(B.lat, B.n, t)];
+        const TileGeo g = tile_geo<TY, TZ>(L, t);
+
+        if (use_tma) {
+            if (!mbar_wait_bounded(&S.mbar, phase)) {
+                if (tid == 0) atomicOr(W.status, STATUS_TMA_TIMEOUT);
+                return;
+            }
+            phase ^= 1u;
+        } else {
+            cp_async_wait_all();
+        }
+        __syncthreads();
+
+        // occupancy words by warp ballot (phi > 0, Sec. 2; zero-filled sites are medium)
+        for (int rr = wid; rr < R; rr += NW) {
+            const uint32_t w = __ballot_sync(0xffffffffu, S.phi[rr * 32 + lane] > 0.0f);
+            if (lane == 0) S.m[rr] = w;
+        }
+        __syncthreads();
+        if (t + gridDim.x < ntiles) issue_load(t + gridDim.x);   // overlaps the labelling below
+
+        const int r = tid, ly = r % TY, lz = r / TY;
+        const uint32_t m = S.m[r];
+        const uint32_t rs = run_starts(m);
+        W.mask[t * R + r] = m;
+
+        // a2: run ids (row-major), union lists, unions
+        int total;
+        const int rb = block_exscan<NT>(__popc(rs), S.warp_tmp, total);
+        S.rbase[r] = rb;
+        for (int i = r; i < total; i += NT) S.par[i] = i;
+        for (int i = r; i < total; i += NT) S.bflag[i] = 0;
+
+        // y-neighbours: one union per overlapping run pair of rows (y-1, y)
+        const uint32_t osy = ly > 0 ? run_starts(m & S.m[r - 1]) : 0u;
+        int ny_tot;
+        const int yb = block_exscan<NT>(__popc(osy), S.warp_tmp, ny_tot);
+        if (osy) {
+            const uint32_t mq = S.m[r - 1];
+            const uint32_t rsq = run_starts(mq);
+            const int rbq = S.rbase[r - 1];
+            uint32_t w = osy;
+            int j = yb;
+            while (w) {
+                const int x = __ffs(w) - 1;
+                w &= w - 1;
+                S.aux[j++] = (run_of(rb, rs, x) << 16) | run_of(rbq, rsq, x);
             }
         }
-    }
-    __syncthreads();
-    W.mask[t * R + threadIdx.x] = S.m[threadIdx.x];
+        __syncthreads();
+        for (int i = tid; i < ny_tot; i += NT) {
+            const uint32_t p = (uint32_t)S.aux[i];
+            s_union(S.par, (int)(p >> 16), (int)(p & 0xffffu), total, W.status);
+        }
+        __syncthreads();
 
-    tile_local_label<TY, TZ>(S, g, W.status);
+        // z-neighbours
+        const uint32_t osz = lz > 0 ? run_starts(m & S.m[r - TY]) : 0u;
+        int nz_tot;
+        const int zb = block_exscan<NT>(__popc(osz), S.warp_tmp, nz_tot);
+        if (osz) {
+            const uint32_t mq = S.m[r - TY];
+            const uint32_t rsq = run_starts(mq);
+            const int rbq = S.rbase[r - TY];
+            uint32_t w = osz;
+            int j = zb;
+            while (w) {
+                const int x = __ffs(w) - 1;
+                w &= w - 1;
+                S.aux[j++] = (run_of(rb, rs, x) << 16) | run_of(rbq, rsq, x);
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < nz_tot; i += NT) {
+            const uint32_t p = (uint32_t)S.aux[i];
+            s_union(S.par, (int)(p >> 16), (int)(p & 0xffffu), total, W.status);
+        }
+        __syncthreads();
 
-    const int r = threadIdx.x;
-    if (r == 0) {
-        const int base = atomicAdd(W.npieces, S.nbound);
-        S.base = base;
-        W.tinfo[t] = make_int2(base, S.nbound);
-    }
-    __syncthreads();
-    const int base = S.base;
+        // periodic edges inside the tile (an axis that fits in one tile)
+        if (g.wrapX || g.wrapY || g.wrapZ) {
+            if (m) {
+                if (g.wrapY && ly == g.lastY && ly > 0)
+                    join_rows(S.par, m, rb, S.m[r - ly], S.rbase[r - ly], total, W.status);
+                if (g.wrapZ && lz == g.lastZ && lz > 0)
+                    join_rows(S.par, m, rb, S.m[r - lz * TY], S.rbase[r - lz * TY], total, W.status);
+                if (g.wrapX && g.lastX > 0 && (m & 1u) && ((m >> g.lastX) & 1u))
+                    s_union(S.par, rb, run_of(rb, rs, g.lastX), total, W.status);
+            }
+            __syncthreads();
+        }
 
-    // boundary pieces into the global table; interior roots counted per row segment
-    const int ly = r % TY, lz = r / TY;
-    if (ly <= g.lastY && lz <= g.lastZ) {
-        const uint32_t m = S.m[r];
-        uint32_t w = run_starts(m);
-        int id = S.rbase[r];
-        int interior = 0;
-        const int site_row = ((g.z0 + lz) * L.ny + (g.y0 + ly)) * L.nx + g.x0;
-        while (w) {
-            const int x = __ffs(w) - 1;
-            w &= w - 1;
-            if (S.par[id] == id) {
-                if (is_boundary(S.bflag, id)) {
-                    const int pid = base + S.kmap[id];
+        // full compression (par[i] = root, the piece's first run), piece sizes and
+        // boundary flags (a piece touching a face with a neighbour tile).  The finds
+        // are read-only, so storing final roots while others still search is safe.
+        // Consecutive runs of one piece in a row are summed before one shared add.
+        for (int i = tid; i < total; i += NT) S.aux[i] = 0;
+        __syncthreads();
+        if (m) {
+            const bool face_row = (ly == 0 && g.extYlo) || (ly == g.lastY && g.extYhi) ||
+                                  (lz == 0 && g.extZlo) || (lz == g.lastZ && g.extZhi);
+            uint32_t w = rs;
+            int id = rb;
+            int cur = -1, acc = 0;
+            while (w) {
+                const int x0 = __ffs(w) - 1;
+                w &= w - 1;
+                const int len = run_len(m, x0);
+                const int root = s_find_ro(S.par, id, total, W.status);
+                S.par[id] = root;
+                if (face_row || (x0 == 0 && g.extXlo) || (g.extXhi && x0 <= g.lastX && x0 + len - 1 >= g.lastX))
+                    S.bflag[root] = 1;
+                if (root != cur) {
+                    if (cur >= 0) atomicAdd(&S.aux[cur], acc);
+                    cur = root;
+                    acc = 0;
+                }
+                acc += len;
+                ++id;
+            }
+            atomicAdd(&S.aux[cur], acc);
+        }
+        __syncthreads();
+
+        // number the boundary roots in run order; par[root] = -1 - k marks them
+        const int per = (total + NT - 1) / NT;
+        const int i0 = tid * per;
+        int cnt = 0;
+        for (int j = 0; j < per; ++j) {
+            const int i = i0 + j;
+            if (i < total && S.par[i] == i && S.bflag[i]) ++cnt;
+        }
+        int nb;
+        int k = block_exscan<NT>(cnt, S.warp_tmp, nb);
+        for (int j = 0; j < per; ++j) {
+            const int i = i0 + j;
+            if (i < total && S.par[i] == i && S.bflag[i]) S.par[i] = -1 - (k++);
+        }
+        const int base = (int)(t * SH::MAX_BOUNDARY);   // fixed slice of the piece table
+        if (tid == 0) W.tinfo[t] = make_int4(base, nb, total, 0);
+        __syncthreads();
+
+        // boundary pieces into the global table; interior roots counted per row segment
+        if (ly <= g.lastY && lz <= g.lastZ) {
+            uint32_t w = rs;
+            int id = rb;
+            int interior = 0;
+            const int site_row = ((g.z0 + lz) * L.ny + (g.y0 + ly)) * L.nx + g.x0;
+            while (w) {
+                const int x = __ffs(w) - 1;
+                w &= w - 1;
+                const int v = S.par[id];
+                if (v < 0) {
+                    const int pid = base + (-1 - v);
                     W.parent[pid] = pid;
                     W.key[pid] = site_row + x;
                     W.psize[pid] = S.aux[id];
-                } else {
+                } else if (v == id) {
                     ++interior;
                 }
+                ++id;
             }
-            ++id;
+            const int64_t seg = L.seg0 + ((int64_t)(g.z0 + lz) * L.ny + (g.y0 + ly)) * L.nbx + g.bx;
+            W.cnt[seg] = (uint32_t)interior;
         }
-        const int64_t seg = L.seg0 + ((int64_t)(g.z0 + lz) * L.ny + (g.y0 + ly)) * L.nbx + g.bx;
-        W.cnt[seg] = (uint32_t)interior;
-    }
 
-    // face summaries: boundary number of the piece holding each face site
-    uint16_t *F = W.face + t * SH::FACE_STRIDE;
-    auto site_k = [&](int row, int x) -> uint16_t {
-        const uint32_t m = S.m[row];
-        if (!((m >> x) & 1u)) return FACE_NONE;
-        return (uint16_t)S.kmap[S.par[run_of(S.rbase[row], run_starts(m), x)]];
-    };
-    if (g.extXlo) F[SH::OFF_LX + r] = site_k(r, 0);
-    if (g.extXhi) F[SH::OFF_HX + r] = site_k(r, g.lastX);
-    for (int e = r; e < TX * TZ; e += NT) {
-        const int fz = e / TX, x = e % TX;
-        if (g.extYlo) F[SH::OFF_LY + e] = site_k(fz * TY, x);
-        if (g.extYhi) F[SH::OFF_HY + e] = site_k(fz * TY + g.lastY, x);
-    }
-    for (int e = r; e < TX * TY; e += NT) {
-        const int fy = e / TX, x = e % TX;
-        if (g.extZlo) F[SH::OFF_LZ + e] = site_k(fy, x);
-        if (g.extZhi) F[SH::OFF_HZ + e] = site_k(g.lastZ * TY + fy, x);
+        // one code per run (CODE_* encoding)
+        uint16_t *C = W.codes + t * MR;
+        for (int i = tid; i < total; i += NT) {
+            const int v = S.par[i];
+            uint16_t c;
+            if (v < 0) {
+                c = (uint16_t)(CODE_BOUNDARY | CODE_ROOT | (-1 - v));
+            } else if (v == i) {
+                c = (uint16_t)(CODE_ROOT | S.aux[i]);
+            } else {
+                const int w2 = S.par[v];
+                c = w2 < 0 ? (uint16_t)(CODE_BOUNDARY | (-1 - w2)) : (uint16_t)v;
+            }
+            C[i] = c;
+        }
+
+        // face summaries: boundary number of the piece holding each face site
+        uint16_t *F = W.face + t * SH::FACE_STRIDE;
+        auto site_k = [&](int row, int x) -> uint16_t {
+            const uint32_t mm = S.m[row];
+            if (!((mm >> x) & 1u)) return FACE_NONE;
+            return (uint16_t)piece_k(S.par, run_of(S.rbase[row], run_starts(mm), x));
+        };
+        if (g.extXlo) F[SH::OFF_LX + r] = site_k(r, 0);
+        if (g.extXhi) F[SH::OFF_HX + r] = site_k(r, g.lastX);
+        for (int e = r; e < TX * TZ; e += NT) {
+            const int fz = e / TX, x = e % TX;
+            if (g.extYlo) F[SH::OFF_LY + e] = site_k(fz * TY, x);
+            if (g.extYhi) F[SH::OFF_HY + e] = site_k(fz * TY + g.lastY, x);
+        }
+        for (int e = r; e < TX * TY; e += NT) {
+            const int fy = e / TX, x = e % TX;
+            if (g.extZlo) F[SH::OFF_LZ + e] = site_k(fy, x);
+            if (g.extZhi) F[SH::OFF_HZ + e] = site_k(g.lastZ * TY + fy, x);
+        }
+        __syncthreads();
     }
 }
 
@@ -154,9 +328,8 @@ __global__ void __launch_bounds__(TY * TZ)
 k_face_merge(const __grid_constant__ LatBatch<NL> B, Work W) {
     using SH = TileShape<TY, TZ>;
     const int64_t t = blockIdx.x;
-    const int lat = (NL == 1) ? 0 : find_lattice(B.lat, B.n, t);
-    const LatDev &L = B.lat[lat];
-    const TileGeo g = tile_geo<TY, TZ>(L, lat, t);
+    const LatDev &L = B.lat[(NL == 1) ? 0 : find_lattice(B.lat, B.n, t)];
+    const TileGeo g = tile_geo<TY, TZ>(L, t);
     const int base = W.tinfo[t].x;
     const uint16_t *F = W.face + t * SH::FACE_STRIDE;
 
@@ -183,7 +356,9 @@ k_face_merge(const __grid_constant__ LatBatch<NL> B, Work W) {
 }
 
 // --------------------------------------------------------------------------------------
-// K3: piece finalize (one warp per tile)
+// K3: piece finalize (one warp per tile).  Size additions into the same cluster
+// root are combined per warp first, because the percolating cluster collects
+// pieces from most tiles.
 // --------------------------------------------------------------------------------------
 template <int NL>
 __global__ void __launch_bounds__(256)
@@ -191,22 +366,36 @@ k_piece_finalize(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles)
     const int64_t t = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (t >= ntiles) return;
     const int lane = threadIdx.x & 31;
-    const int2 ti = W.tinfo[t];
+    const int4 ti = W.tinfo[t];
     if (ti.y == 0) return;
-    const int lat = (NL == 1) ? 0 : find_lattice(B.lat, B.n, t);
-    const LatDev &L = B.lat[lat];
-    for (int j = lane; j < ti.y; j += 32) {
+    const LatDev &L = B.lat[(NL == 1) ? 0 : find_lattice(B.lat, B.n, t)];
+    for (int j0 = 0; j0 < ti.y; j0 += 32) {
+        const int j = j0 + lane;
+        const bool valid = j < ti.y;
         const int pid = ti.x + j;
-        const int root = g_find_ro(W.parent, pid, W.piece_cap, W.status);
-        if (root != pid) {
-            __stcg(W.parent + pid, root);
-            atomicAdd(W.psize + root, W.psize[pid]);
-        } else {
-            const int k = W.key[pid];
-            const int y = (k / L.nx) % L.ny, z = (k / L.nx) / L.ny, x = k % L.nx;
-            const int64_t seg = L.seg0 + ((int64_t)z * L.ny + y) * L.nbx + (x >> 5);
-            atomicAdd(W.cnt + seg, 1u);
+        int root = -1, add = 0;
+        if (valid) {
+            root = g_find_ro(W.parent, pid, W.piece_cap, W.status);
+            if (root != pid) {
+                __stcg(W.parent + pid, root);
+                add = W.psize[pid];
+                // from here on key[pid] is the cluster's label and psize[pid] < 0 marks a
+                // non-root; only roots' keys are read by other threads, and a root's key
+                // never changes
+                W.key[pid] = __ldcg(W.key + root);
+                W.psize[pid] = -1;
+            } else {
+                const int k = W.key[pid];
+                const int q = k / L.nx, x = k - q * L.nx;
+                const int y = q % L.ny, z = q / L.ny;
+                const int64_t seg = L.seg0 + ((int64_t)z * L.ny + y) * L.nbx + (x >> 5);
+                atomicAdd(W.cnt + seg, 1u);
+            }
         }
+        const int target = (valid && root != pid) ? root : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, target);
+        const int sum = (int)__reduce_add_sync(peers, (unsigned)add);
+        if (target >= 0 && lane == __ffs(peers) - 1) atomicAdd(W.psize + target, sum);
     }
 }
 
@@ -302,15 +491,14 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_apply(const uint32_t *cnt, int
 #pragma unroll
     for (int j = 0; j < SCAN_PER; ++j) {
         const int64_t i = b0 + j;
-        if (i < n) pre[i] = run;
-        if (i == n) pre[i] = run;   // total at pre[n]
+        if (i <= n) pre[i] = run;   // pre[n] = total
         run += v[j];
     }
 }
 
 // per-lattice: cluster count from the prefix, clear the histogram
 template <int NL>
-__global__ void k_lattice_finish(const __grid_constant__ LatBatch<NL> B, Work W, int64_t nseg_total) {
+__global__ void k_lattice_finish(const __grid_constant__ LatBatch<NL> B, Work W) {
     const int l = blockIdx.x;
     if (l >= B.n) return;
     const LatDev &L = B.lat[l];
@@ -322,118 +510,186 @@ __global__ void k_lattice_finish(const __grid_constant__ LatBatch<NL> B, Work W,
 }
 
 // --------------------------------------------------------------------------------------
-// K4: flatten
+// K4: flatten (decode run codes; no union-find)
 // --------------------------------------------------------------------------------------
+template <int TY, int TZ>
+struct FlatSmem {
+    using SH = TileShape<TY, TZ>;
+    alignas(128) int32_t stage[SH::SITES];    // labels [lz][ly][x] (TMA store source)
+    uint16_t code[SH::MAXRUNS];
+    uint16_t runpos[SH::MAXRUNS];             // (row << 5) | x0 of every run
+    int gl[SH::MAX_BOUNDARY];                 // label of each boundary piece's cluster
+    int gsize[SH::MAX_BOUNDARY];              // cluster size if the piece is the cluster root, else -1
+    int warp_tmp[32];
+    int hist[32];
+};
+
+template <int TY, int TZ>
+__device__ __forceinline__ int site_of(const TileGeo &g, const LatDev &L, int pos) {
+    const int row = pos >> 5, x = pos & 31;
+    return ((g.z0 + row / TY) * L.ny + (g.y0 + row % TY)) * L.nx + g.x0 + x;
+}
+
 template <int TY, int TZ, int NL>
 __global__ void __launch_bounds__(TY * TZ)
-k_flatten(const __grid_constant__ LatBatch<NL> B, Work W) {
+k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapPair tm, Work W, int64_t ntiles) {
     using SH = TileShape<TY, TZ>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TileSmem<TY, TZ> &S = *reinterpret_cast<TileSmem<TY, TZ> *>(smem_raw);
-    constexpr int R = SH::R, NW = SH::NT / 32;
+    constexpr int R = SH::R, NT = SH::NT, NW = NT / 32, MR = SH::MAXRUNS;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    FlatSmem<TY, TZ> &S = *reinterpret_cast<FlatSmem<TY, TZ> *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const bool use_tma = (NL == 1) && tm.valid;
 
-    const int64_t t = blockIdx.x;
-    const int lat = (NL == 1) ? 0 : find_lattice(B.lat, B.n, t);
-    const LatDev &L = B.lat[lat];
-    const TileGeo g = tile_geo<TY, TZ>(L, lat, t);
-    const int r = threadIdx.x;
-    S.m[r] = W.mask[t * R + r];
-    if (r < 32) S.hist[r] = 0;
-    __syncthreads();
+    if (tid < 32) S.hist[tid] = 0;
+    int cur_lat = -1;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int lat = (NL == 1) ? 0 : find_lattice(B.lat, B.n, t);
+        const LatDev &L = B.lat[lat];
+        const TileGeo g = tile_geo<TY, TZ>(L, t);
+        const int4 ti = W.tinfo[t];
+        const int base = ti.x, nb = ti.y, total = ti.z;
+        const int r = tid, ly = r % TY, lz = r / TY;
+        const uint32_t m = W.mask[t * R + r];
+        const uint32_t rs = run_starts(m);
 
-    tile_local_label<TY, TZ>(S, g, W.status);
+        if (use_tma && tid == 0) bulk_wait_read0();    // the previous tile's store has read S.stage
+        __syncthreads();
+        if (lat != cur_lat) {                          // uniform: flush the histogram per lattice
+            if (cur_lat >= 0 && tid < 32 && S.hist[tid] && B.lat[cur_lat].hist)
+                atomicAdd(reinterpret_cast<unsigned long long *>(B.lat[cur_lat].hist) + tid,
+                          (unsigned long long)S.hist[tid]);
+            __syncthreads();
+            if (tid < 32) S.hist[tid] = 0;
+            cur_lat = lat;
+        }
 
-    const int base = W.tinfo[t].x;
-    const int ly = r % TY, lz = r / TY;
-    if (ly <= g.lastY && lz <= g.lastZ) {
-        const uint32_t m = S.m[r];
-        uint32_t w = run_starts(m);
-        if (w) {
-            const int64_t seg = L.seg0 + ((int64_t)(g.z0 + lz) * L.ny + (g.y0 + ly)) * L.nbx + g.bx;
-            int64_t rank = (int64_t)W.pre[seg] - (int64_t)W.pre[L.seg0];
-            const int site_row = ((g.z0 + lz) * L.ny + (g.y0 + ly)) * L.nx + g.x0;
-            int id = S.rbase[r];
+        const uint16_t *C = W.codes + t * MR;
+        for (int i = tid; i < total; i += NT) S.code[i] = C[i];
+        for (int k = tid; k < nb; k += NT) {
+            S.gl[k] = __ldg(W.key + base + k);       // cluster label (written by piece_finalize)
+            S.gsize[k] = __ldg(W.psize + base + k);  // cluster size at the root piece, else -1
+        }
+        for (int i = tid; i < SH::SITES / 4; i += NT)
+            reinterpret_cast<int4 *>(S.stage)[i] = make_int4(-1, -1, -1, -1);
+        int tot2;
+        const int rb = block_exscan<NT>(__popc(rs), S.warp_tmp, tot2);
+        {
+            uint32_t w = rs;
+            int id = rb;
             while (w) {
-                const int x = __ffs(w) - 1;
+                const int x0 = __ffs(w) - 1;
                 w &= w - 1;
-                if (S.par[id] == id) {
-                    int lab, size = 0;
-                    bool root;
-                    if (is_boundary(S.bflag, id)) {
-                        const int pid = base + S.kmap[id];
-                        const int gr = __ldg(W.parent + pid);
-                        lab = __ldg(W.key + gr);
-                        root = gr == pid;
-                        if (root) size = __ldg(W.psize + pid);
-                    } else {
-                        lab = site_row + x;
-                        root = true;
-                        size = S.aux[id];
-                    }
-                    if (root) {
-                        if (rank < L.sizes_cap) L.sizes[rank] = size;
-                        atomicAdd(&S.hist[31 - __clz(size)], 1);
-                        ++rank;
-                    }
-                    S.aux[id] = lab;
-                }
-                ++id;
+                S.runpos[id++] = (uint16_t)((r << 5) | x0);
             }
         }
-    }
-    __syncthreads();
+        __syncthreads();
 
-    // a5: labels, one coalesced 128-byte row store per warp step
-    {
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        const int64_t sxy = (int64_t)L.nx * L.ny;
-        int32_t *out = L.labels + (int64_t)g.z0 * sxy + (int64_t)g.y0 * L.nx + g.x0 + lane;
-        const bool xin = lane <= g.lastX;
-        for (int rr = wid; rr < R; rr += NW) {
-            const int yy = rr % TY, zz = rr / TY;
-            if (!xin || yy > g.lastY || zz > g.lastZ) continue;
-            const uint32_t m = S.m[rr];
-            int lab = -1;
-            if ((m >> lane) & 1u) lab = S.aux[S.par[run_of(S.rbase[rr], run_starts(m), lane)]];
-            __stcs(out + (int64_t)zz * sxy + (int64_t)yy * L.nx, lab);
+        // a4-a7: one pass over the runs of each row in x order: cluster roots get
+        // their rank, size and histogram entry; every run writes its label
+        const bool valid_row = ly <= g.lastY && lz <= g.lastZ;
+        int64_t rank = 0;
+        if (rs && valid_row) {
+            const int64_t seg = L.seg0 + ((int64_t)(g.z0 + lz) * L.ny + (g.y0 + ly)) * L.nbx + g.bx;
+            rank = (int64_t)W.pre[seg] - (int64_t)W.pre[L.seg0];
+        }
+        const int site_row = ((g.z0 + lz) * L.ny + (g.y0 + ly)) * L.nx + g.x0;
+        const int steps = __reduce_max_sync(0xffffffffu, __popc(rs));
+        uint32_t w = rs;
+        int id = rb;
+        for (int j = 0; j < steps; ++j) {
+            int size = -1;
+            if (w) {
+                const int x0 = __ffs(w) - 1;
+                w &= w - 1;
+                const int c = S.code[id++];
+                int lab;
+                if (c & CODE_BOUNDARY) {
+                    const int k = c & CODE_LOW;
+                    lab = S.gl[k];
+                    if (c & CODE_ROOT) size = S.gsize[k];
+                } else if (c & CODE_ROOT) {
+                    lab = site_row + x0;
+                    size = c & CODE_LOW;
+                } else {
+                    lab = site_of<TY, TZ>(g, L, S.runpos[c]);
+                }
+                if (size > 0) {
+                    if (rank < L.sizes_cap) L.sizes[rank] = size;
+                    ++rank;
+                }
+                const int len = run_len(m, x0);
+                int *dst = S.stage + r * 32 + x0;
+                for (int x = 0; x < len; ++x) dst[x] = lab;
+            }
+            // histogram bin, combined per warp (many clusters share the small bins)
+            const int bin = size > 0 ? 31 - __clz(size) : -1;
+            const unsigned grp = __match_any_sync(0xffffffffu, bin);
+            if (bin >= 0 && lane == __ffs(grp) - 1) atomicAdd(&S.hist[bin], __popc(grp));
+        }
+        if (use_tma) fence_proxy_async();
+        __syncthreads();
+        if (use_tma) {
+            if (tid == 0) {
+                tma_store_3d(&tm.labels, S.stage, g.x0, g.y0, g.z0);
+                bulk_commit();
+            }
+        } else {
+            const int64_t sxy = (int64_t)L.nx * L.ny;
+            int32_t *out = L.labels + (int64_t)g.z0 * sxy + (int64_t)g.y0 * L.nx + g.x0 + lane;
+            if (lane <= g.lastX)
+                for (int rr = wid; rr < R; rr += NW) {
+                    const int yy = rr % TY, zz = rr / TY;
+                    if (yy <= g.lastY && zz <= g.lastZ)
+                        __stcs(out + (int64_t)zz * sxy + (int64_t)yy * L.nx, S.stage[rr * 32 + lane]);
+                }
         }
     }
-    if (L.hist && r < 32 && S.hist[r])
-        atomicAdd(reinterpret_cast<unsigned long long *>(L.hist) + r, (unsigned long long)S.hist[r]);
+    if (use_tma && tid == 0) bulk_wait0();
+    __syncthreads();
+    if (cur_lat >= 0 && tid < 32 && S.hist[tid] && B.lat[cur_lat].hist)
+        atomicAdd(reinterpret_cast<unsigned long long *>(B.lat[cur_lat].hist) + tid, (unsigned long long)S.hist[tid]);
 }
 
 // --------------------------------------------------------------------------------------
 // launch sequence
 // --------------------------------------------------------------------------------------
-template <int TY, int TZ>
-static size_t tile_smem_bytes() { return sizeof(TileSmem<TY, TZ>); }
+template <typename K>
+static int persistent_grid(K kernel, int threads, size_t smem, int64_t ntiles) {
+    int dev = 0, nsm = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem);
+    int64_t g = (int64_t)nsm * (per > 0 ? per : 1);
+    if (g > ntiles) g = ntiles;
+    return (int)(g > 0 ? g : 1);
+}
 
 template <int TY, int TZ, int NL>
-static cudaError_t launch_all(const LatDev *lats, int n, const Plan &P, const Work &W, cudaStream_t st,
-                              cudaEvent_t *ev) {
+static cudaError_t launch_all(const LatDev *lats, int n, const Plan &P, const Work &W, const TmapPair &tm,
+                              cudaStream_t st, cudaEvent_t *ev) {
     using SH = TileShape<TY, TZ>;
     LatBatch<NL> B;
     B.n = n;
     B.pad_ = 0;
     for (int i = 0; i < n; ++i) B.lat[i] = lats[i];
-    const size_t smem = tile_smem_bytes<TY, TZ>();
+    const size_t smem1 = sizeof(LabelSmem<TY, TZ>), smem4 = sizeof(FlatSmem<TY, TZ>);
     cudaError_t e;
-    static bool attr_done = false;
-    if (!attr_done) {
-        e = cudaFuncSetAttribute(k_tile_label<TY, TZ, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static int grid1 = 0, grid4 = 0;
+    if (!grid1) {
+        e = cudaFuncSetAttribute(k_tile_label<TY, TZ, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_flatten<TY, TZ, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_flatten<TY, TZ, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4);
         if (e != cudaSuccess) return e;
-        attr_done = true;
+        grid1 = persistent_grid(k_tile_label<TY, TZ, NL>, SH::NT, smem1, INT32_MAX);
+        grid4 = persistent_grid(k_flatten<TY, TZ, NL>, SH::NT, smem4, INT32_MAX);
     }
-    e = cudaMemsetAsync(W.npieces, 0, sizeof(int32_t), st);
-    if (e != cudaSuccess) return e;
-    const unsigned grid = (unsigned)P.ntiles;
+    const unsigned g1 = (unsigned)(P.ntiles < grid1 ? P.ntiles : grid1);
+    const unsigned g4 = (unsigned)(P.ntiles < grid4 ? P.ntiles : grid4);
     auto mark = [&](int i) { if (ev) cudaEventRecord(ev[i], st); };
     mark(0);
-    k_tile_label<TY, TZ, NL><<<grid, SH::NT, smem, st>>>(B, W);
+    k_tile_label<TY, TZ, NL><<<g1, SH::NT, smem1, st>>>(B, tm, W, P.ntiles);
     mark(1);
-    k_face_merge<TY, TZ, NL><<<grid, SH::NT, 0, st>>>(B, W);
+    k_face_merge<TY, TZ, NL><<<(unsigned)P.ntiles, SH::NT, 0, st>>>(B, W);
     mark(2);
     k_piece_finalize<NL><<<(unsigned)((P.ntiles + 7) / 8), 256, 0, st>>>(B, W, P.ntiles);
     mark(3);
@@ -442,18 +698,18 @@ static cudaError_t launch_all(const LatDev *lats, int n, const Plan &P, const Wo
     k_scan_blocks<<<1, 1024, 0, st>>>(W.bsum, nb);
     k_scan_apply<<<(unsigned)nb, SCAN_NT, 0, st>>>(W.cnt, P.nseg, W.bsum, W.pre);
     mark(4);
-    k_lattice_finish<NL><<<(unsigned)n, 32, 0, st>>>(B, W, P.nseg);
+    k_lattice_finish<NL><<<(unsigned)n, 32, 0, st>>>(B, W);
     mark(5);
-    k_flatten<TY, TZ, NL><<<grid, SH::NT, smem, st>>>(B, W);
+    k_flatten<TY, TZ, NL><<<g4, SH::NT, smem4, st>>>(B, tm, W, P.ntiles);
     mark(6);
     return cudaGetLastError();
 }
 
 template <int TY, int TZ>
-static cudaError_t launch_shape(const LatDev *lats, int n, const Plan &P, const Work &W, cudaStream_t st,
-                                cudaEvent_t *ev) {
-    if (n == 1) return launch_all<TY, TZ, 1>(lats, n, P, W, st, ev);
-    return launch_all<TY, TZ, MAX_LAT_PER_LAUNCH>(lats, n, P, W, st, ev);
+static cudaError_t launch_shape(const LatDev *lats, int n, const Plan &P, const Work &W, const TmapPair &tm,
+                                cudaStream_t st, cudaEvent_t *ev) {
+    if (n == 1) return launch_all<TY, TZ, 1>(lats, n, P, W, tm, st, ev);
+    return launch_all<TY, TZ, MAX_LAT_PER_LAUNCH>(lats, n, P, W, tm, st, ev);
 }
 
 template <int TY, int TZ>
@@ -462,9 +718,9 @@ static void shape_info(TileInfo &ti) {
     ti.ty = TY;
     ti.tz = TZ;
     ti.rows = SH::R;
+    ti.maxruns = SH::MAXRUNS;
     ti.face_stride = SH::FACE_STRIDE;
     ti.max_boundary = SH::MAX_BOUNDARY;
-    ti.smem = sizeof(TileSmem<TY, TZ>);
 }
 
 bool tile_info(int ty, int tz, TileInfo &ti) {
@@ -475,12 +731,12 @@ bool tile_info(int ty, int tz, TileInfo &ti) {
     return false;
 }
 
-cudaError_t launch_label(int ty, int tz, const LatDev *lats, int n, const Plan &P, const Work &W, cudaStream_t st,
-                         cudaEvent_t *ev) {
-    if (ty == 8 && tz == 8) return launch_shape<8, 8>(lats, n, P, W, st, ev);
-    if (ty == 16 && tz == 8) return launch_shape<16, 8>(lats, n, P, W, st, ev);
-    if (ty == 16 && tz == 16) return launch_shape<16, 16>(lats, n, P, W, st, ev);
-    if (ty == 32 && tz == 8) return launch_shape<32, 8>(lats, n, P, W, st, ev);
+cudaError_t launch_label(int ty, int tz, const LatDev *lats, int n, const Plan &P, const Work &W, const TmapPair &tm,
+                         cudaStream_t st, cudaEvent_t *ev) {
+    if (ty == 8 && tz == 8) return launch_shape<8, 8>(lats, n, P, W, tm, st, ev);
+    if (ty == 16 && tz == 8) return launch_shape<16, 8>(lats, n, P, W, tm, st, ev);
+    if (ty == 16 && tz == 16) return launch_shape<16, 16>(lats, n, P, W, tm, st, ev);
+    if (ty == 32 && tz == 8) return launch_shape<32, 8>(lats, n, P, W, tm, st, ev);
     return cudaErrorInvalidValue;
 }
 

@@ -9,15 +9,16 @@ namespace hk {
 
 struct LatDev;
 struct Work;
+struct TmapPair;
 
 constexpr int MAX_LAT_PER_LAUNCH = 128;
 
 struct TileInfo {
     int ty, tz;
     int rows;            // tile rows (ty * tz), one 32-bit occupancy word each
+    int maxruns;         // run-code entries per tile
     int face_stride;     // uint16 face entries per tile
     int max_boundary;    // bound on boundary pieces per tile
-    size_t smem;         // dynamic shared memory of the tile kernels
 };
 
 struct Plan {
@@ -26,11 +27,14 @@ struct Plan {
     int64_t piece_cap;   // ntiles * max_boundary
 };
 
-bool tile_info(int ty, int tz, TileInfo &ti);
 constexpr int NUM_PASSES = 6;   // tile_label, face_merge, piece_finalize, scan, lattice_finish, flatten
 
-// ev: NUM_PASSES + 1 events recorded around the passes, or nullptr
-cudaError_t launch_label(int ty, int tz, const LatDev *lats, int n, const Plan &P, const Work &W, cudaStream_t st,
-                         cudaEvent_t *ev);
+bool tile_info(int ty, int tz, TileInfo &ti);
+
+// ev: NUM_PASSES + 1 events recorded around the passes, or nullptr.  tm: tensor
+// maps for the single-lattice TMA path (tm->valid == 0 selects the cp.async /
+// plain-store path).
+cudaError_t launch_label(int ty, int tz, const LatDev *lats, int n, const Plan &P, const Work &W,
+                         const TmapPair &tm, cudaStream_t st, cudaEvent_t *ev);
 
 }  // namespace hk
