@@ -130,6 +130,33 @@ int hk_label_host(hk_ctx *ctx, const float *phi_host, int nx, int ny, int nz, co
                   int32_t *labels_host, int64_t *sizes_host, int64_t sizes_cap,
                   int64_t *hist_host, int64_t *n_clusters_host, void *stream);
 
+/* hk_label without any device allocation, for callers that cannot allocate
+ * device memory (for example a simulation that has handed all free device
+ * memory to its own allocator, or a loop in which a cudaMalloc/cudaFree would
+ * synchronise the device and stall the caller's other streams).  The paper has
+ * no counterpart; this is a property of the library, not of the method.
+ *
+ * Arguments, layout, results and the capacity rule are those of hk_label, on
+ * the current CUDA device, with no context.  Instead of a context workspace
+ * the call uses one file-scope __device__ scratch array of
+ * HK_NOALLOC_SCRATCH_BYTES (64 MiB), which every GPU that loads the library
+ * holds until the process exits; that is enough for lattices up to about 16
+ * million sites (256^3).  A lattice whose scratch would not fit is rejected
+ * with HK_ERR_TOO_LARGE before anything is enqueued.  The call never calls
+ * cudaMalloc, cudaFree or any allocating library routine.
+ *
+ * The first call on a device looks up the array's device address on that
+ * device (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Every call shares the one array and it keeps the last call's
+ * contents (each call rewrites what it reads), so calls that overlap on the
+ * GPU -- on different streams, or from different host threads -- race and
+ * must be serialised by the caller.  It uses the plain-load path (no TMA).
+ * Errors: HK_ERR_ARG, HK_ERR_TOO_LARGE, HK_ERR_CUDA, HK_ERR_CAPACITY. */
+#define HK_NOALLOC_SCRATCH_BYTES (64u << 20)
+int hk_label_noalloc(const float *phi, int nx, int ny, int nz, const int periodic[3],
+                     int32_t *labels_out, int64_t *sizes_out, int64_t sizes_cap,
+                     int64_t *hist_out, int64_t *n_clusters_out, void *stream);
+
 /* Select the tile shape (rows per tile along y and z; x tiles are always 32
  * sites wide).  Supported: (ty, tz) in {(8,8), (16,8), (16,16), (32,8)}; 0,0 =
  * the library default.  Applies to later calls on this context.

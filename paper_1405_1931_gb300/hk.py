@@ -20,7 +20,7 @@ HK_OK, HK_ERR_ARG, HK_ERR_TOO_LARGE, HK_ERR_CAPACITY = 0, 1, 2, 3
 HK_ERR_CUDA, HK_ERR_TIMEOUT, HK_ERR_NOMEM = 4, 5, 6
 
 EXPORTED = ("hk_create", "hk_destroy", "hk_workspace_bytes", "hk_reserve", "hk_label", "hk_label_batched",
-            "hk_label_host", "hk_set_tile", "hk_set_timing", "hk_get_timing", "hk_sync_status", "hk_last_cuda_error", "hk_strerror",
+            "hk_label_host", "hk_set_tile", "hk_set_timing", "hk_get_timing", "hk_sync_status", "hk_last_cuda_error", "hk_strerror", "hk_label_noalloc",
             "hk_gen_iid", "hk_gen_spheres", "hk_gen_capsule")
 
 _lock = threading.Lock()
@@ -61,6 +61,7 @@ def load():
             "hk_label": (I, [P, P, I, I, I, P, P, P, I64, P, P, P]),
             "hk_label_batched": (I, [P, ctypes.POINTER(hk_lattice), I, P]),
             "hk_label_host": (I, [P, P, I, I, I, P, P, P, I64, P, P, P]),
+            "hk_label_noalloc": (I, [P, I, I, I, P, P, P, I64, P, P, P]),
             "hk_set_tile": (I, [P, I, I]),
             "hk_set_timing": (I, [P, I]),
             "hk_get_timing": (I, [P, ctypes.POINTER(ctypes.c_float), I, ctypes.POINTER(ctypes.c_int)]),
@@ -120,6 +121,15 @@ def hk_label_host(ctx, phi_host, nx, ny, nz, periodic, labels_host, sizes_host, 
                   n_clusters_host, stream=0) -> int:
     return load().hk_label_host(ctx, phi_host, nx, ny, nz, _per(periodic), labels_host, sizes_host,
                                 int(sizes_cap), hist_host, n_clusters_host, stream)
+
+
+def hk_label_noalloc(phi, nx, ny, nz, periodic, labels_out, sizes_out, sizes_cap, hist_out, n_clusters_out,
+                     stream=0) -> int:
+    return load().hk_label_noalloc(phi, nx, ny, nz, _per(periodic), labels_out, sizes_out, int(sizes_cap),
+                                   hist_out, n_clusters_out, stream)
+
+
+NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
 def hk_set_tile(ctx, ty, tz) -> int:
