@@ -23,7 +23,8 @@ constexpr uint16_t FACE_NONE = 0xFFFF;
 //   CODE_BOUNDARY | k               a run of boundary piece k of the tile
 //   CODE_BOUNDARY | CODE_ROOT | k   the first run of boundary piece k
 //   CODE_ROOT | size                the first run of an interior piece (its size, <= 8192)
-//   r (< CODE_ROOT)                 another run of the interior piece whose first run is r
+//   (row << 5) | x0  (< CODE_ROOT)  another run of the interior piece whose first run starts
+//                                   at tile row `row`, column x0
 constexpr uint16_t CODE_BOUNDARY = 0x8000;
 constexpr uint16_t CODE_ROOT = 0x4000;
 constexpr uint16_t CODE_LOW = 0x3fff;

@@ -41,16 +41,22 @@ struct LabelSmem {
     int rbase[SH::R];                      // first run id of each row
     int par[SH::MAXRUNS];                  // union-find over run ids; after numbering a
                                            // boundary root i holds -1 - (its boundary number)
-    int aux[SH::MAXRUNS];                  // union pair lists, then piece sizes at roots
-    uint8_t bflag[SH::MAXRUNS];            // boundary flag per root (plain stores of 1)
+    int aux[SH::MAXRUNS];                  // union pair lists, then per root: size + AUX_FACE * (runs
+                                           // touching an external face)
     int warp_tmp[32];
     uint64_t mbar;
 };
 
+constexpr int AUX_FACE = 1 << 14;   // > any piece size (a tile has at most 8192 sites)
+constexpr int ROOTPOS = 1 << 16;    // par[root] = ROOTPOS | (row << 5 | x0) marks an interior root
+
 // Decode of par[] after numbering: boundary number of run i's piece, or -1 if interior.
+// par[i] is -1 - k for a boundary root, ROOTPOS | position for an interior root, and
+// the root's run id otherwise.
 __device__ __forceinline__ int piece_k(const int *par, int i) {
     const int v = par[i];
-    if (v < 0) return -1 - v;            // i is a boundary root
+    if (v < 0) return -1 - v;
+    if (v >= ROOTPOS) return -1;
     const int w = par[v];
     return w < 0 ? -1 - w : -1;
 }
@@ -130,7 +136,6 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ Tma
         const int rb = block_exscan<NT>(__popc(rs), S.warp_tmp, total);
         S.rbase[r] = rb;
         for (int i = r; i < total; i += NT) S.par[i] = i;
-        for (int i = r; i < total; i += NT) S.bflag[i] = 0;
 
         // y-neighbours: one union per overlapping run pair of rows (y-1, y)
         const uint32_t osy = ly > 0 ? run_starts(m & S.m[r - 1]) : 0u;
@@ -191,33 +196,39 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ Tma
             __syncthreads();
         }
 
-        // full compression (par[i] = root, the piece's first run), piece sizes and
-        // boundary flags (a piece touching a face with a neighbour tile).  The finds
-        // are read-only, so storing final roots while others still search is safe.
-        // Consecutive runs of one piece in a row are summed before one shared add.
-        for (int i = tid; i < total; i += NT) S.aux[i] = 0;
+        // full compression, one run id per thread: par[i] = root (the piece's first
+        // run).  The finds are read-only, so storing final roots while others still
+        // search is safe.
+        for (int i = tid; i < total; i += NT) {
+            S.par[i] = s_find_ro(S.par, i, total, W.status);
+            S.aux[i] = 0;
+        }
         __syncthreads();
+
+        // piece sizes and boundary marks in one shared add per (row, piece): a piece
+        // is a boundary piece iff one of its runs touches a tile face that has a
+        // neighbour tile, which adds AUX_FACE (sizes are < AUX_FACE)
         if (m) {
             const bool face_row = (ly == 0 && g.extYlo) || (ly == g.lastY && g.extYhi) ||
                                   (lz == 0 && g.extZlo) || (lz == g.lastZ && g.extZhi);
             uint32_t w = rs;
             int id = rb;
-            int cur = -1, acc = 0;
+            int cur = S.par[id], acc = 0;
             while (w) {
                 const int x0 = __ffs(w) - 1;
                 w &= w - 1;
                 const int len = run_len(m, x0);
-                const int root = s_find_ro(S.par, id, total, W.status);
-                S.par[id] = root;
-                if (face_row || (x0 == 0 && g.extXlo) || (g.extXhi && x0 <= g.lastX && x0 + len - 1 >= g.lastX))
-                    S.bflag[root] = 1;
+                const int root = S.par[id];
+                if (root == id) S.par[id] = ROOTPOS | (r << 5) | x0;   // only this thread reads it
+                ++id;
+                const bool touch =
+                    face_row || (x0 == 0 && g.extXlo) || (g.extXhi && x0 <= g.lastX && x0 + len - 1 >= g.lastX);
                 if (root != cur) {
-                    if (cur >= 0) atomicAdd(&S.aux[cur], acc);
+                    atomicAdd(&S.aux[cur], acc);
                     cur = root;
                     acc = 0;
                 }
-                acc += len;
-                ++id;
+                acc += len + (touch ? AUX_FACE : 0);
             }
             atomicAdd(&S.aux[cur], acc);
         }
@@ -229,13 +240,13 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ Tma
         int cnt = 0;
         for (int j = 0; j < per; ++j) {
             const int i = i0 + j;
-            if (i < total && S.par[i] == i && S.bflag[i]) ++cnt;
+            if (i < total && S.par[i] >= ROOTPOS && S.aux[i] >= AUX_FACE) ++cnt;
         }
         int nb;
         int k = block_exscan<NT>(cnt, S.warp_tmp, nb);
         for (int j = 0; j < per; ++j) {
             const int i = i0 + j;
-            if (i < total && S.par[i] == i && S.bflag[i]) S.par[i] = -1 - (k++);
+            if (i < total && S.par[i] >= ROOTPOS && S.aux[i] >= AUX_FACE) S.par[i] = -1 - (k++);
         }
         const int base = (int)(t * SH::MAX_BOUNDARY);   // fixed slice of the piece table
         if (tid == 0) W.tinfo[t] = make_int4(base, nb, total, 0);
@@ -255,8 +266,8 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ Tma
                     const int pid = base + (-1 - v);
                     W.parent[pid] = pid;
                     W.key[pid] = site_row + x;
-                    W.psize[pid] = S.aux[id];
-                } else if (v == id) {
+                    W.psize[pid] = S.aux[id] & (AUX_FACE - 1);
+                } else if (v >= ROOTPOS) {
                     ++interior;
                 }
                 ++id;
@@ -272,11 +283,11 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ Tma
             uint16_t c;
             if (v < 0) {
                 c = (uint16_t)(CODE_BOUNDARY | CODE_ROOT | (-1 - v));
-            } else if (v == i) {
-                c = (uint16_t)(CODE_ROOT | S.aux[i]);
+            } else if (v >= ROOTPOS) {
+                c = (uint16_t)(CODE_ROOT | (S.aux[i] & (AUX_FACE - 1)));
             } else {
                 const int w2 = S.par[v];
-                c = w2 < 0 ? (uint16_t)(CODE_BOUNDARY | (-1 - w2)) : (uint16_t)v;
+                c = w2 < 0 ? (uint16_t)(CODE_BOUNDARY | (-1 - w2)) : (uint16_t)(w2 & (ROOTPOS - 1));
             }
             C[i] = c;
         }
@@ -517,7 +528,6 @@ struct FlatSmem {
     using SH = TileShape<TY, TZ>;
     alignas(128) int32_t stage[SH::SITES];    // labels [lz][ly][x] (TMA store source)
     uint16_t code[SH::MAXRUNS];
-    uint16_t runpos[SH::MAXRUNS];             // (row << 5) | x0 of every run
     int gl[SH::MAX_BOUNDARY];                 // label of each boundary piece's cluster
     int gsize[SH::MAX_BOUNDARY];              // cluster size if the piece is the cluster root, else -1
     int warp_tmp[32];
@@ -572,17 +582,7 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapPa
         for (int i = tid; i < SH::SITES / 4; i += NT)
             reinterpret_cast<int4 *>(S.stage)[i] = make_int4(-1, -1, -1, -1);
         int tot2;
-        const int rb = block_exscan<NT>(__popc(rs), S.warp_tmp, tot2);
-        {
-            uint32_t w = rs;
-            int id = rb;
-            while (w) {
-                const int x0 = __ffs(w) - 1;
-                w &= w - 1;
-                S.runpos[id++] = (uint16_t)((r << 5) | x0);
-            }
-        }
-        __syncthreads();
+        const int rb = block_exscan<NT>(__popc(rs), S.warp_tmp, tot2);   // ends with a barrier
 
         // a4-a7: one pass over the runs of each row in x order: cluster roots get
         // their rank, size and histogram entry; every run writes its label
@@ -593,38 +593,39 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapPa
             rank = (int64_t)W.pre[seg] - (int64_t)W.pre[L.seg0];
         }
         const int site_row = ((g.z0 + lz) * L.ny + (g.y0 + ly)) * L.nx + g.x0;
-        const int steps = __reduce_max_sync(0xffffffffu, __popc(rs));
+        int small[4] = {0, 0, 0, 0};   // histogram bins 0..3, combined per warp below
         uint32_t w = rs;
         int id = rb;
-        for (int j = 0; j < steps; ++j) {
-            int size = -1;
-            if (w) {
-                const int x0 = __ffs(w) - 1;
-                w &= w - 1;
-                const int c = S.code[id++];
-                int lab;
-                if (c & CODE_BOUNDARY) {
-                    const int k = c & CODE_LOW;
-                    lab = S.gl[k];
-                    if (c & CODE_ROOT) size = S.gsize[k];
-                } else if (c & CODE_ROOT) {
-                    lab = site_row + x0;
-                    size = c & CODE_LOW;
-                } else {
-                    lab = site_of<TY, TZ>(g, L, S.runpos[c]);
-                }
-                if (size > 0) {
-                    if (rank < L.sizes_cap) L.sizes[rank] = size;
-                    ++rank;
-                }
-                const int len = run_len(m, x0);
-                int *dst = S.stage + r * 32 + x0;
-                for (int x = 0; x < len; ++x) dst[x] = lab;
+        while (w) {
+            const int x0 = __ffs(w) - 1;
+            w &= w - 1;
+            const int c = S.code[id++];
+            int lab, size = -1;
+            if (c & CODE_BOUNDARY) {
+                const int k = c & CODE_LOW;
+                lab = S.gl[k];
+                if (c & CODE_ROOT) size = S.gsize[k];
+            } else if (c & CODE_ROOT) {
+                lab = site_row + x0;
+                size = c & CODE_LOW;
+            } else {
+                lab = site_of<TY, TZ>(g, L, c);
             }
-            // histogram bin, combined per warp (many clusters share the small bins)
-            const int bin = size > 0 ? 31 - __clz(size) : -1;
-            const unsigned grp = __match_any_sync(0xffffffffu, bin);
-            if (bin >= 0 && lane == __ffs(grp) - 1) atomicAdd(&S.hist[bin], __popc(grp));
+            if (size > 0) {
+                if (rank < L.sizes_cap) L.sizes[rank] = size;
+                ++rank;
+                const int bin = 31 - __clz(size);
+                if (bin < 4) ++small[bin];
+                else atomicAdd(&S.hist[bin], 1);
+            }
+            const int len = run_len(m, x0);
+            int *dst = S.stage + r * 32 + x0;
+            for (int x = 0; x < len; ++x) dst[x] = lab;
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int s = (int)__reduce_add_sync(0xffffffffu, (unsigned)small[b]);
+            if (lane == 0 && s) atomicAdd(&S.hist[b], s);
         }
         if (use_tma) fence_proxy_async();
         __syncthreads();
