@@ -168,13 +168,14 @@ int hk_set_tile(hk_ctx *ctx, int ty, int tz);
  * of 64 event sets; the host waits for a call 64 calls old before reusing its
  * set).  hk_get_timing synchronises on the timed calls still in flight and
  * writes up to max_n per-pass AVERAGE durations in milliseconds over all timed
- * calls since timing was enabled to ms_out (host), in pass order: tile_label,
- * face_merge, piece_finalize, scan (three kernels), lattice_finish, flatten;
+ * calls since timing was enabled to ms_out (host), in pass order: occupancy,
+ * tile_label, face_merge, piece_finalize, scan (three kernels), lattice_finish,
+ * flatten;
  * *n_out gets the number of passes.  For a batch split into several launch
  * chunks each chunk counts as one call.  Timing adds event records only;
  * results are unchanged.  Errors: HK_ERR_ARG (no timed call yet, NULL ctx or
  * ms_out), HK_ERR_CUDA. */
-#define HK_NUM_PASSES 6
+#define HK_NUM_PASSES 7
 int hk_set_timing(hk_ctx *ctx, int enable);
 int hk_get_timing(hk_ctx *ctx, float *ms_out, int max_n, int *n_out);
 

@@ -1,12 +1,11 @@
 // hk_kernels.cu -- the labelling passes.
 //
-//   K1 tile_label     persistent: stream phi tiles into shared memory (TMA
-//                     tensor loads, prefetching the next tile while the
-//                     current one is labelled), write the occupancy mask,
-//                     label each tile locally (Sec. 2's rules become
-//                     union-find over x-runs), register boundary pieces, and
-//                     write one code per run, the face summaries and the
-//                     per-row count of interior cluster roots.
+//   K0 occupancy      stream phi once (coalesced row loads) and write the
+//                     occupancy mask phi > 0, one 32-bit word per tile row.
+//   K1 tile_label     label each tile from its mask words (Sec. 2's rules
+//                     become union-find over x-runs), register boundary
+//                     pieces, and write one code per run, the face summaries
+//                     and the per-row count of interior cluster roots.
 //   K2 face_merge     join boundary pieces across tile faces and periodic
 //                     edges: the intra-GPU counterpart of Sec. 3's halo
 //                     equivalences, resolved directly on a global union-find
@@ -33,18 +32,117 @@ struct LatBatch {
 // --------------------------------------------------------------------------------------
 // K1: tile labelling
 // --------------------------------------------------------------------------------------
+// --------------------------------------------------------------------------------------
+// K0: occupancy.  One warp per tile streams phi row by row (one coalesced 128-byte
+// load per row, 16 rows in flight per warp) and keeps phi > 0 (Sec. 2) as one
+// 32-bit word per tile row, written tile-major.  Sites outside the lattice count
+// as medium.
+// --------------------------------------------------------------------------------------
+template <int TY, int TZ, int NL>
+__global__ void __launch_bounds__(256) k_occupancy(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
+    using SH = TileShape<TY, TZ>;
+    constexpr int R = SH::R, U = 16;
+    const int lane = threadIdx.x & 31;
+    const int64_t t = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (t >= ntiles) return;
+    const LatDev &L = B.lat[(NL == 1) ? 0 : find_lattice(B.lat, B.n, t)];
+    const TileGeo g = tile_geo<TY, TZ>(L, t);
+    const int64_t sxy = (int64_t)L.nx * L.ny;
+    const float *base = L.phi + (int64_t)g.z0 * sxy + (int64_t)g.y0 * L.nx + g.x0 + lane;
+    const bool xin = lane <= g.lastX;
+    uint32_t *out = W.mask + t * R;
+    for (int r0 = 0; r0 < R; r0 += 32) {        // lane j keeps the word of row r0 + j
+        uint32_t mine = 0;
+#pragma unroll
+        for (int u0 = 0; u0 < 32; u0 += U) {
+            float v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int rr = r0 + u0 + u, ly = rr % TY, lz = rr / TY;
+                v[u] = (xin && ly <= g.lastY && lz <= g.lastZ)
+                           ? __ldcs(base + (int64_t)lz * sxy + (int64_t)ly * L.nx) : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t w = __ballot_sync(0xffffffffu, v[u] > 0.0f);
+                if (lane == u0 + u) mine = w;
+            }
+        }
+        out[r0 + lane] = mine;
+    }
+}
+
+// K0 with TMA (single lattice, 16-byte aligned rows): persistent, a ring of two
+// tile buffers per CTA filled by cp.async.bulk.tensor loads completed on
+// mbarriers; while one tile is converted the next is in flight.
+template <int TY, int TZ>
+struct OccSmem {
+    using SH = TileShape<TY, TZ>;
+    alignas(128) float buf[2][SH::SITES];
+    uint64_t bar[2];
+};
+
+template <int TY, int TZ>
+__global__ void __launch_bounds__(256) k_occupancy_tma(const __grid_constant__ TmapPair tm, const __grid_constant__ LatBatch<1> B,
+                                                       Work W, int64_t ntiles) {
+    using SH = TileShape<TY, TZ>;
+    constexpr int R = SH::R;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    OccSmem<TY, TZ> &S = *reinterpret_cast<OccSmem<TY, TZ> *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const LatDev &L = B.lat[0];
+    if (tid == 0) {
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int64_t t, int s) {
+        const TileGeo g = tile_geo<TY, TZ>(L, t);
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&S.bar[s], SH::SITES * 4);
+        tma_load_3d(S.buf[s], &tm.phi, &S.bar[s], g.x0, g.y0, g.z0);
+    };
+    const int64_t t0 = blockIdx.x, step = gridDim.x;
+    if (tid == 0) {
+        if (t0 < ntiles) issue(t0, 0);
+        if (t0 + step < ntiles) issue(t0 + step, 1);
+    }
+    int k = 0;
+    for (int64_t t = t0; t < ntiles; t += step, ++k) {
+        const int s = k & 1;
+        if (!mbar_wait_bounded(&S.bar[s], (uint32_t)((k >> 1) & 1))) {
+            if (tid == 0) atomicOr(W.status, STATUS_TMA_TIMEOUT);
+            return;
+        }
+        // warp w converts rows [32 w', 32 w' + 32) in turns; lane j keeps row 32 w' + j
+        for (int r0 = wid * 32; r0 < R; r0 += 32 * (256 / 32)) {
+            uint32_t mine = 0;
+#pragma unroll 8
+            for (int j = 0; j < 32; ++j) {
+                const uint32_t w = __ballot_sync(0xffffffffu, S.buf[s][(r0 + j) * 32 + lane] > 0.0f);
+                if (lane == j) mine = w;
+            }
+            W.mask[t * R + r0 + lane] = mine;
+        }
+        __syncthreads();                       // every warp is done with buffer s
+        if (tid == 0 && t + 2 * step < ntiles) issue(t + 2 * step, s);
+    }
+}
+
+// --------------------------------------------------------------------------------------
+// K1: tile labelling from the occupancy words (one tile per CTA)
+// --------------------------------------------------------------------------------------
 template <int TY, int TZ>
 struct LabelSmem {
     using SH = TileShape<TY, TZ>;
-    alignas(128) float phi[SH::SITES];     // tile of phi, [lz][ly][x] (TMA / cp.async destination)
     uint32_t m[SH::R];                     // occupancy word of each row
     int rbase[SH::R];                      // first run id of each row
-    int par[SH::MAXRUNS];                  // union-find over run ids; after numbering a
-                                           // boundary root i holds -1 - (its boundary number)
+    int par[SH::MAXRUNS];                  // union-find over run ids; see piece_k for the
+                                           // encodings after numbering
     int aux[SH::MAXRUNS];                  // union pair lists, then per root: size + AUX_FACE * (runs
                                            // touching an external face)
     int warp_tmp[32];
-    uint64_t mbar;
 };
 
 constexpr int AUX_FACE = 1 << 14;   // > any piece size (a tile has at most 8192 sites)
@@ -62,74 +160,22 @@ __device__ __forceinline__ int piece_k(const int *par, int i) {
 }
 
 template <int TY, int TZ, int NL>
-__global__ void __launch_bounds__(TY * TZ)
-k_tile_label(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapPair tm, Work W, int64_t ntiles) {
+__global__ void __launch_bounds__(TY * TZ, 1280 / (TY * TZ))
+k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
     using SH = TileShape<TY, TZ>;
-    constexpr int R = SH::R, NT = SH::NT, NW = NT / 32, MR = SH::MAXRUNS;
+    constexpr int R = SH::R, NT = SH::NT, MR = SH::MAXRUNS;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     LabelSmem<TY, TZ> &S = *reinterpret_cast<LabelSmem<TY, TZ> *>(smem_raw);
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const bool use_tma = (NL == 1) && tm.valid;
+    const int tid = threadIdx.x;
 
-    if (tid == 0) {
-        mbar_init(&S.mbar, 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-
-    // a1: start the copy of tile t's phi into S.phi (zero fill outside the lattice)
-    auto issue_load = [&](int64_t t) {
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const LatDev &L = B.lat[(NL == 1) ? 0 : find_lattice(B.lat, B.n, t)];
         const TileGeo g = tile_geo<TY, TZ>(L, t);
-        if (use_tma) {
-            if (tid == 0) {
-                fence_proxy_async();
-                mbar_arrive_expect_tx(&S.mbar, SH::SITES * 4);
-                tma_load_3d(S.phi, &tm.phi, &S.mbar, g.x0, g.y0, g.z0);
-            }
-        } else {
-            const int64_t sxy = (int64_t)L.nx * L.ny;
-            for (int e = tid; e < SH::SITES; e += NT) {
-                const int x = e & 31, rr = e >> 5, ly = rr % TY, lz = rr / TY;
-                const bool ok = x <= g.lastX && ly <= g.lastY && lz <= g.lastZ;
-                const float *src =
-                    ok ? L.phi + (int64_t)(g.z0 + lz) * sxy + (int64_t)(g.y0 + ly) * L.nx + g.x0 + x : L.phi;
-                cp_async4(&S.phi[e], src, ok ? 4 : 0);
-            }
-            cp_async_commit();
-        }
-    };
-
-    uint32_t phase = 0;
-    int64_t t = blockIdx.x;
-    if (t < ntiles) issue_load(t);
-    for (; t < ntiles; t += gridDim.x) {
-        const LatDev &L = B.lat[(NL == 1) ? 0 : find_lattice(B.lat, B.n, t)];
-        const TileGeo g = tile_geo<TY, TZ>(L, t);
-
-        if (use_tma) {
-            if (!mbar_wait_bounded(&S.mbar, phase)) {
-                if (tid == 0) atomicOr(W.status, STATUS_TMA_TIMEOUT);
-                return;
-            }
-            phase ^= 1u;
-        } else {
-            cp_async_wait_all();
-        }
-        __syncthreads();
-
-        // occupancy words by warp ballot (phi > 0, Sec. 2; zero-filled sites are medium)
-        for (int rr = wid; rr < R; rr += NW) {
-            const uint32_t w = __ballot_sync(0xffffffffu, S.phi[rr * 32 + lane] > 0.0f);
-            if (lane == 0) S.m[rr] = w;
-        }
-        __syncthreads();
-        if (t + gridDim.x < ntiles) issue_load(t + gridDim.x);   // overlaps the labelling below
 
         const int r = tid, ly = r % TY, lz = r / TY;
-        const uint32_t m = S.m[r];
+        const uint32_t m = W.mask[t * R + r];
+        S.m[r] = m;
         const uint32_t rs = run_starts(m);
-        W.mask[t * R + r] = m;
 
         // a2: run ids (row-major), union lists, unions
         int total;
@@ -561,6 +607,14 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapPa
         const int r = tid, ly = r % TY, lz = r / TY;
         const uint32_t m = W.mask[t * R + r];
         const uint32_t rs = run_starts(m);
+        const bool valid_row = ly <= g.lastY && lz <= g.lastZ;
+        // rank base of this row: issued early, used after the barriers below
+        uint32_t pre_row = 0, pre_lat = 0;
+        if (rs && valid_row) {
+            const int64_t seg = L.seg0 + ((int64_t)(g.z0 + lz) * L.ny + (g.y0 + ly)) * L.nbx + g.bx;
+            pre_row = W.pre[seg];
+            pre_lat = W.pre[L.seg0];
+        }
 
         if (use_tma && tid == 0) bulk_wait_read0();    // the previous tile's store has read S.stage
         __syncthreads();
@@ -586,14 +640,9 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapPa
 
         // a4-a7: one pass over the runs of each row in x order: cluster roots get
         // their rank, size and histogram entry; every run writes its label
-        const bool valid_row = ly <= g.lastY && lz <= g.lastZ;
-        int64_t rank = 0;
-        if (rs && valid_row) {
-            const int64_t seg = L.seg0 + ((int64_t)(g.z0 + lz) * L.ny + (g.y0 + ly)) * L.nbx + g.bx;
-            rank = (int64_t)W.pre[seg] - (int64_t)W.pre[L.seg0];
-        }
+        int64_t rank = (int64_t)pre_row - (int64_t)pre_lat;
         const int site_row = ((g.z0 + lz) * L.ny + (g.y0 + ly)) * L.nx + g.x0;
-        int small[4] = {0, 0, 0, 0};   // histogram bins 0..3, combined per warp below
+        int h0 = 0, h1 = 0, h2 = 0, h3 = 0;   // histogram bins 0..3, combined per warp below
         uint32_t w = rs;
         int id = rb;
         while (w) {
@@ -615,17 +664,27 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapPa
                 if (rank < L.sizes_cap) L.sizes[rank] = size;
                 ++rank;
                 const int bin = 31 - __clz(size);
-                if (bin < 4) ++small[bin];
-                else atomicAdd(&S.hist[bin], 1);
+                h0 += bin == 0;
+                h1 += bin == 1;
+                h2 += bin == 2;
+                h3 += bin == 3;
+                if (bin >= 4) atomicAdd(&S.hist[bin], 1);
             }
             const int len = run_len(m, x0);
             int *dst = S.stage + r * 32 + x0;
             for (int x = 0; x < len; ++x) dst[x] = lab;
         }
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const int s = (int)__reduce_add_sync(0xffffffffu, (unsigned)small[b]);
-            if (lane == 0 && s) atomicAdd(&S.hist[b], s);
+        {
+            const int s0 = (int)__reduce_add_sync(0xffffffffu, (unsigned)h0);
+            const int s1 = (int)__reduce_add_sync(0xffffffffu, (unsigned)h1);
+            const int s2 = (int)__reduce_add_sync(0xffffffffu, (unsigned)h2);
+            const int s3 = (int)__reduce_add_sync(0xffffffffu, (unsigned)h3);
+            if (lane == 0) {
+                if (s0) atomicAdd(&S.hist[0], s0);
+                if (s1) atomicAdd(&S.hist[1], s1);
+                if (s2) atomicAdd(&S.hist[2], s2);
+                if (s3) atomicAdd(&S.hist[3], s3);
+            }
         }
         if (use_tma) fence_proxy_async();
         __syncthreads();
@@ -675,34 +734,50 @@ static cudaError_t launch_all(const LatDev *lats, int n, const Plan &P, const Wo
     for (int i = 0; i < n; ++i) B.lat[i] = lats[i];
     const size_t smem1 = sizeof(LabelSmem<TY, TZ>), smem4 = sizeof(FlatSmem<TY, TZ>);
     cudaError_t e;
-    static int grid1 = 0, grid4 = 0;
-    if (!grid1) {
+    static int grid4 = 0;
+    if (!grid4) {
         e = cudaFuncSetAttribute(k_tile_label<TY, TZ, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(k_flatten<TY, TZ, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4);
         if (e != cudaSuccess) return e;
-        grid1 = persistent_grid(k_tile_label<TY, TZ, NL>, SH::NT, smem1, INT32_MAX);
         grid4 = persistent_grid(k_flatten<TY, TZ, NL>, SH::NT, smem4, INT32_MAX);
     }
-    const unsigned g1 = (unsigned)(P.ntiles < grid1 ? P.ntiles : grid1);
     const unsigned g4 = (unsigned)(P.ntiles < grid4 ? P.ntiles : grid4);
     auto mark = [&](int i) { if (ev) cudaEventRecord(ev[i], st); };
     mark(0);
-    k_tile_label<TY, TZ, NL><<<g1, SH::NT, smem1, st>>>(B, tm, W, P.ntiles);
+    if constexpr (NL == 1) {
+        if (tm.valid) {
+            static int grid0 = 0;
+            const size_t smem0 = sizeof(OccSmem<TY, TZ>);
+            if (!grid0) {
+                e = cudaFuncSetAttribute(k_occupancy_tma<TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem0);
+                if (e != cudaSuccess) return e;
+                grid0 = persistent_grid(k_occupancy_tma<TY, TZ>, 256, smem0, INT32_MAX);
+            }
+            const unsigned g0 = (unsigned)(P.ntiles < grid0 ? P.ntiles : grid0);
+            k_occupancy_tma<TY, TZ><<<g0, 256, smem0, st>>>(tm, B, W, P.ntiles);
+        } else {
+            k_occupancy<TY, TZ, NL><<<(unsigned)((P.ntiles + 7) / 8), 256, 0, st>>>(B, W, P.ntiles);
+        }
+    } else {
+        k_occupancy<TY, TZ, NL><<<(unsigned)((P.ntiles + 7) / 8), 256, 0, st>>>(B, W, P.ntiles);
+    }
     mark(1);
-    k_face_merge<TY, TZ, NL><<<(unsigned)P.ntiles, SH::NT, 0, st>>>(B, W);
+    k_tile_label<TY, TZ, NL><<<(unsigned)P.ntiles, SH::NT, smem1, st>>>(B, W, P.ntiles);
     mark(2);
-    k_piece_finalize<NL><<<(unsigned)((P.ntiles + 7) / 8), 256, 0, st>>>(B, W, P.ntiles);
+    k_face_merge<TY, TZ, NL><<<(unsigned)P.ntiles, SH::NT, 0, st>>>(B, W);
     mark(3);
+    k_piece_finalize<NL><<<(unsigned)((P.ntiles + 7) / 8), 256, 0, st>>>(B, W, P.ntiles);
+    mark(4);
     const int64_t nb = (P.nseg + SCAN_CH) / SCAN_CH;   // covers index nseg (the total)
     k_scan_reduce<<<(unsigned)nb, SCAN_NT, 0, st>>>(W.cnt, P.nseg, W.bsum);
     k_scan_blocks<<<1, 1024, 0, st>>>(W.bsum, nb);
     k_scan_apply<<<(unsigned)nb, SCAN_NT, 0, st>>>(W.cnt, P.nseg, W.bsum, W.pre);
-    mark(4);
-    k_lattice_finish<NL><<<(unsigned)n, 32, 0, st>>>(B, W);
     mark(5);
-    k_flatten<TY, TZ, NL><<<g4, SH::NT, smem4, st>>>(B, tm, W, P.ntiles);
+    k_lattice_finish<NL><<<(unsigned)n, 32, 0, st>>>(B, W);
     mark(6);
+    k_flatten<TY, TZ, NL><<<g4, SH::NT, smem4, st>>>(B, tm, W, P.ntiles);
+    mark(7);
     return cudaGetLastError();
 }
 

@@ -27,7 +27,7 @@ struct Plan {
     int64_t piece_cap;   // ntiles * max_boundary
 };
 
-constexpr int NUM_PASSES = 6;   // tile_label, face_merge, piece_finalize, scan, lattice_finish, flatten
+constexpr int NUM_PASSES = 7;   // occupancy, tile_label, face_merge, piece_finalize, scan, lattice_finish, flatten
 
 bool tile_info(int ty, int tz, TileInfo &ti);
 

@@ -136,7 +136,7 @@ def hk_set_tile(ctx, ty, tz) -> int:
     return load().hk_set_tile(ctx, ty, tz)
 
 
-PASS_NAMES = ("tile_label", "face_merge", "piece_finalize", "scan", "lattice_finish", "flatten")
+PASS_NAMES = ("occupancy", "tile_label", "face_merge", "piece_finalize", "scan", "lattice_finish", "flatten")
 
 
 def hk_set_timing(ctx, enable: bool) -> int:
