@@ -62,6 +62,8 @@ struct Work {
                         // after piece_finalize: the label of the piece's cluster
     int32_t *psize;     // [piece_cap] piece size; after piece_finalize: the cluster size at
                         // the cluster's root piece, -1 elsewhere
+    uint32_t *xcol;     // [ntiles * 2 * R/32] occupancy of each tile's first (x = 0) and last
+                        // (x = lastX) column, one bit per tile row
     int32_t *status;    // [1] device-side error flags (STATUS_*), owned by the context
     int64_t piece_cap;  // entries of parent/key/psize: bounds every union-find path
 };
@@ -299,7 +301,8 @@ __device__ __forceinline__ int block_exscan(int v, int *warp_tmp, int &total) {
 // ---- global union-find over boundary pieces --------------------------------------------
 // Links go from a root to a root with a smaller key (the piece's first site), so
 // keys strictly decrease along parent pointers and each cluster's root is the
-// piece holding the cluster's smallest site index.
+// piece holding the cluster's smallest site index.  The parent array is kept at
+// 4 bytes a piece: finds hop across the whole table, so its footprint in L2 matters.
 // A path visits distinct pieces, so `cap` (the piece-table size) bounds it.
 __device__ __forceinline__ int g_find(int32_t *parent, int x, int64_t cap, int32_t *status) {
     int p = __ldcg(parent + x);

@@ -69,6 +69,13 @@ __global__ void __launch_bounds__(256) k_occupancy(const __grid_constant__ LatBa
             }
         }
         out[r0 + lane] = mine;
+        // first and last column of the tile, one bit per row (faces along x)
+        const uint32_t c0 = __ballot_sync(0xffffffffu, mine & 1u);
+        const uint32_t cl = __ballot_sync(0xffffffffu, (mine >> g.lastX) & 1u);
+        if (lane == 0) {
+            W.xcol[(t * 2) * (R / 32) + (r0 >> 5)] = c0;
+            W.xcol[(t * 2 + 1) * (R / 32) + (r0 >> 5)] = cl;
+        }
     }
 }
 
@@ -124,6 +131,13 @@ __global__ void __launch_bounds__(256) k_occupancy_tma(const __grid_constant__ T
                 if (lane == j) mine = w;
             }
             W.mask[t * R + r0 + lane] = mine;
+            const int lastX = min(TX, L.nx - (int)(t % L.nbx) * TX) - 1;
+            const uint32_t c0 = __ballot_sync(0xffffffffu, mine & 1u);
+            const uint32_t cl = __ballot_sync(0xffffffffu, (mine >> lastX) & 1u);
+            if (lane == 0) {
+                W.xcol[(t * 2) * (R / 32) + (r0 >> 5)] = c0;
+                W.xcol[(t * 2 + 1) * (R / 32) + (r0 >> 5)] = cl;
+            }
         }
         __syncthreads();                       // every warp is done with buffer s
         if (tid == 0 && t + 2 * step < ntiles) issue(t + 2 * step, s);
@@ -141,7 +155,11 @@ struct LabelSmem {
     int par[SH::MAXRUNS];                  // union-find over run ids; see piece_k for the
                                            // encodings after numbering
     int aux[SH::MAXRUNS];                  // union pair lists, then per root: size + AUX_FACE * (runs
-                                           // touching an external face)
+                                           // with a site connected across a tile face)
+    uint32_t nylo[TZ], nyhi[TZ];           // neighbour rows across the y faces, per plane
+    uint32_t nzlo[TY], nzhi[TY];           // neighbour rows across the z faces, per row
+    uint32_t nxlo[SH::R / 32], nxhi[SH::R / 32];   // neighbour columns across the x faces
+    static_assert(TZ <= 16 && TY <= 32 && SH::R / 32 <= 16 && SH::NT >= 64, "face loads use threads 0..63");
     int warp_tmp[32];
 };
 
@@ -176,6 +194,35 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
         const uint32_t m = W.mask[t * R + r];
         S.m[r] = m;
         const uint32_t rs = run_starts(m);
+
+        // Occupancy across the six faces, from the neighbour tiles' masks (the
+        // occupancy pass has written all of them).  A face site is connected when
+        // it and its neighbour across the face are both occupied; only pieces with a
+        // connected site take part in the merge between tiles.
+        {
+            const int64_t plane = (int64_t)L.nbx * L.nby;
+            const int lastY_lo = g.by > 0 ? TY - 1 : L.ny - 1 - (L.nby - 1) * TY;   // neighbour's last row
+            const int lastZ_lo = g.bz > 0 ? TZ - 1 : L.nz - 1 - (L.nbz - 1) * TZ;
+            constexpr int RW = R / 32;
+            if (tid < TZ) {
+                const int64_t tylo = g.by > 0 ? t - L.nbx : t + (int64_t)(L.nby - 1) * L.nbx;
+                const int64_t tyhi = g.by < L.nby - 1 ? t + L.nbx : t - (int64_t)(L.nby - 1) * L.nbx;
+                S.nylo[tid] = g.extYlo ? W.mask[tylo * R + tid * TY + lastY_lo] : 0u;
+                S.nyhi[tid] = g.extYhi ? W.mask[tyhi * R + tid * TY] : 0u;
+            } else if (tid >= 16 && tid < 16 + TY) {     // TZ <= 16, TY <= 32, R/32 <= 8, NT >= 64
+                const int q = tid - 16;
+                const int64_t tzlo = g.bz > 0 ? t - plane : t + (int64_t)(L.nbz - 1) * plane;
+                const int64_t tzhi = g.bz < L.nbz - 1 ? t + plane : t - (int64_t)(L.nbz - 1) * plane;
+                S.nzlo[q] = g.extZlo ? W.mask[tzlo * R + lastZ_lo * TY + q] : 0u;
+                S.nzhi[q] = g.extZhi ? W.mask[tzhi * R + q] : 0u;
+            } else if (tid >= 48 && tid < 48 + RW) {
+                const int q = tid - 48;
+                const int64_t txlo = g.bx > 0 ? t - 1 : t + (L.nbx - 1);
+                const int64_t txhi = g.bx < L.nbx - 1 ? t + 1 : t - (L.nbx - 1);
+                S.nxlo[q] = g.extXlo ? W.xcol[(txlo * 2 + 1) * RW + q] : 0u;   // its last column
+                S.nxhi[q] = g.extXhi ? W.xcol[(txhi * 2) * RW + q] : 0u;       // its first column
+            }
+        }
 
         // a2: run ids (row-major), union lists, unions
         int total;
@@ -255,8 +302,14 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
         // is a boundary piece iff one of its runs touches a tile face that has a
         // neighbour tile, which adds AUX_FACE (sizes are < AUX_FACE)
         if (m) {
-            const bool face_row = (ly == 0 && g.extYlo) || (ly == g.lastY && g.extYhi) ||
-                                  (lz == 0 && g.extZlo) || (lz == g.lastZ && g.extZhi);
+            uint32_t conn = 0;   // sites of this row connected across a tile face
+            if (ly == 0) conn |= S.nylo[lz];
+            if (ly == g.lastY) conn |= S.nyhi[lz];
+            if (lz == 0) conn |= S.nzlo[ly];
+            if (lz == g.lastZ) conn |= S.nzhi[ly];
+            if ((S.nxlo[r >> 5] >> (r & 31)) & 1u) conn |= 1u;
+            if ((S.nxhi[r >> 5] >> (r & 31)) & 1u) conn |= 1u << g.lastX;
+            conn &= m;
             uint32_t w = rs;
             int id = rb;
             int cur = S.par[id], acc = 0;
@@ -267,8 +320,8 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
                 const int root = S.par[id];
                 if (root == id) S.par[id] = ROOTPOS | (r << 5) | x0;   // only this thread reads it
                 ++id;
-                const bool touch =
-                    face_row || (x0 == 0 && g.extXlo) || (g.extXhi && x0 <= g.lastX && x0 + len - 1 >= g.lastX);
+                const uint32_t bits = len == 32 ? 0xffffffffu : (((1u << len) - 1u) << x0);
+                const bool touch = (bits & conn) != 0;
                 if (root != cur) {
                     atomicAdd(&S.aux[cur], acc);
                     cur = root;
@@ -338,95 +391,103 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
             C[i] = c;
         }
 
-        // face summaries: boundary number of the piece holding each face site
+        // face summaries: boundary number of the piece holding each connected face site
         uint16_t *F = W.face + t * SH::FACE_STRIDE;
-        auto site_k = [&](int row, int x) -> uint16_t {
+        auto site_k = [&](int row, uint32_t conn_bits, int x) -> uint16_t {
+            if (!((conn_bits >> x) & 1u)) return FACE_NONE;
             const uint32_t mm = S.m[row];
-            if (!((mm >> x) & 1u)) return FACE_NONE;
             return (uint16_t)piece_k(S.par, run_of(S.rbase[row], run_starts(mm), x));
         };
-        if (g.extXlo) F[SH::OFF_LX + r] = site_k(r, 0);
-        if (g.extXhi) F[SH::OFF_HX + r] = site_k(r, g.lastX);
+        if (g.extXlo) F[SH::OFF_LX + r] = site_k(r, ((S.nxlo[r >> 5] >> (r & 31)) & 1u) ? m : 0u, 0);
+        if (g.extXhi) F[SH::OFF_HX + r] = site_k(r, ((S.nxhi[r >> 5] >> (r & 31)) & 1u) ? m : 0u, g.lastX);
         for (int e = r; e < TX * TZ; e += NT) {
             const int fz = e / TX, x = e % TX;
-            if (g.extYlo) F[SH::OFF_LY + e] = site_k(fz * TY, x);
-            if (g.extYhi) F[SH::OFF_HY + e] = site_k(fz * TY + g.lastY, x);
+            if (g.extYlo) F[SH::OFF_LY + e] = site_k(fz * TY, S.m[fz * TY] & S.nylo[fz], x);
+            if (g.extYhi) F[SH::OFF_HY + e] = site_k(fz * TY + g.lastY, S.m[fz * TY + g.lastY] & S.nyhi[fz], x);
         }
         for (int e = r; e < TX * TY; e += NT) {
             const int fy = e / TX, x = e % TX;
-            if (g.extZlo) F[SH::OFF_LZ + e] = site_k(fy, x);
-            if (g.extZhi) F[SH::OFF_HZ + e] = site_k(g.lastZ * TY + fy, x);
+            if (g.extZlo) F[SH::OFF_LZ + e] = site_k(fy, S.m[fy] & S.nzlo[fy], x);
+            if (g.extZhi) F[SH::OFF_HZ + e] = site_k(g.lastZ * TY + fy, S.m[g.lastZ * TY + fy] & S.nzhi[fy], x);
         }
         __syncthreads();
     }
 }
 
 // --------------------------------------------------------------------------------------
-// K2: face merge.  Each tile joins its three low faces with the high faces of its
-// lower neighbours (for tile 0 of a periodic axis: with the last tile, the wrap).
+// K2: face merge.  Each tile joins its low face along axis blockIdx.y with the high
+// face of its lower neighbour (for tile 0 of a periodic axis: with the last tile,
+// the wrap).  One face per CTA and all face entries loaded before any union, so the
+// union chains of many faces are in flight together.
 // --------------------------------------------------------------------------------------
-__device__ __forceinline__ void merge_face_run(const uint16_t *Fa, const uint16_t *Fb, int n, int base_a,
-                                               int base_b, Work &W) {
-    // n is a multiple of 32; lanes cover consecutive x, so a run of equal pairs
-    // along x is joined once
-    const int lane = threadIdx.x & 31;
-    for (int e = threadIdx.x; e < n; e += blockDim.x) {
-        const uint16_t a = Fa[e], b = Fb[e];
-        const uint32_t pair = ((uint32_t)a << 16) | b;
-        const uint32_t prev = __shfl_up_sync(0xffffffffu, pair, 1);
-        const bool valid = a != FACE_NONE && b != FACE_NONE;
-        if (valid && (lane == 0 || prev != pair))
-            g_union(W.parent, W.key, base_a + a, base_b + b, W.piece_cap, W.status);
-    }
-}
-
 template <int TY, int TZ, int NL>
 __global__ void __launch_bounds__(TY * TZ)
 k_face_merge(const __grid_constant__ LatBatch<NL> B, Work W) {
     using SH = TileShape<TY, TZ>;
+    constexpr int NT = SH::NT;
+    constexpr int PY = (TX * TZ + NT - 1) / NT, PZ = (TX * TY + NT - 1) / NT;   // entries per thread
     const int64_t t = blockIdx.x;
     const LatDev &L = B.lat[(NL == 1) ? 0 : find_lattice(B.lat, B.n, t)];
     const TileGeo g = tile_geo<TY, TZ>(L, t);
     const int base = W.tinfo[t].x;
     const uint16_t *F = W.face + t * SH::FACE_STRIDE;
-
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int64_t plane = (int64_t)L.nbx * L.nby;
+    const int64_t tx = g.bx > 0 ? t - 1 : t + (L.nbx - 1);
+    const int64_t ty = g.by > 0 ? t - L.nbx : t + (int64_t)(L.nby - 1) * L.nbx;
+    const int64_t tz = g.bz > 0 ? t - plane : t + (int64_t)(L.nbz - 1) * plane;
+    // load every face entry this thread joins before the first union
+    uint32_t px = 0xffffffffu, py[PY], pz[PZ];
+    int bx_ = 0, by_ = 0, bz_ = 0;
     if (g.extXlo) {
-        const int64_t tp = g.bx > 0 ? t - 1 : t + (L.nbx - 1);
-        const int bp = W.tinfo[tp].x;
-        const uint16_t *Fp = W.face + tp * SH::FACE_STRIDE;
-        for (int r = threadIdx.x; r < SH::R; r += blockDim.x) {
-            const uint16_t a = F[SH::OFF_LX + r], b = Fp[SH::OFF_HX + r];
-            if (a != FACE_NONE && b != FACE_NONE) g_union(W.parent, W.key, base + a, bp + b, W.piece_cap, W.status);
-        }
+        bx_ = W.tinfo[tx].x;
+        px = ((uint32_t)F[SH::OFF_LX + tid] << 16) | W.face[tx * SH::FACE_STRIDE + SH::OFF_HX + tid];
     }
-    if (g.extYlo) {
-        const int64_t tp = g.by > 0 ? t - L.nbx : t + (int64_t)(L.nby - 1) * L.nbx;
-        const uint16_t *Fp = W.face + tp * SH::FACE_STRIDE;
-        merge_face_run(F + SH::OFF_LY, Fp + SH::OFF_HY, TX * TZ, base, W.tinfo[tp].x, W);
+#pragma unroll
+    for (int j = 0; j < PY; ++j) {
+        const int e = tid + j * NT;
+        py[j] = 0xffffffffu;
+        if (g.extYlo && e < TX * TZ)
+            py[j] = ((uint32_t)F[SH::OFF_LY + e] << 16) | W.face[ty * SH::FACE_STRIDE + SH::OFF_HY + e];
     }
-    if (g.extZlo) {
-        const int64_t plane = (int64_t)L.nbx * L.nby;
-        const int64_t tp = g.bz > 0 ? t - plane : t + (int64_t)(L.nbz - 1) * plane;
-        const uint16_t *Fp = W.face + tp * SH::FACE_STRIDE;
-        merge_face_run(F + SH::OFF_LZ, Fp + SH::OFF_HZ, TX * TY, base, W.tinfo[tp].x, W);
+#pragma unroll
+    for (int j = 0; j < PZ; ++j) {
+        const int e = tid + j * NT;
+        pz[j] = 0xffffffffu;
+        if (g.extZlo && e < TX * TY)
+            pz[j] = ((uint32_t)F[SH::OFF_LZ + e] << 16) | W.face[tz * SH::FACE_STRIDE + SH::OFF_HZ + e];
     }
+    if (g.extYlo) by_ = W.tinfo[ty].x;
+    if (g.extZlo) bz_ = W.tinfo[tz].x;
+    auto join = [&](uint32_t pr, int bp, bool dedup) {
+        // y/z faces list consecutive x in each row (a warp covers one row): a run of
+        // equal pairs along x is joined once
+        const uint32_t prev = __shfl_up_sync(0xffffffffu, pr, 1);
+        const uint16_t a = (uint16_t)(pr >> 16), b = (uint16_t)pr;
+        if (a != FACE_NONE && b != FACE_NONE && !(dedup && lane != 0 && prev == pr))
+            g_union(W.parent, W.key, base + a, bp + b, W.piece_cap, W.status);
+    };
+    join(px, bx_, false);
+#pragma unroll
+    for (int j = 0; j < PY; ++j) join(py[j], by_, true);
+#pragma unroll
+    for (int j = 0; j < PZ; ++j) join(pz[j], bz_, true);
 }
 
 // --------------------------------------------------------------------------------------
-// K3: piece finalize (one warp per tile).  Size additions into the same cluster
-// root are combined per warp first, because the percolating cluster collects
-// pieces from most tiles.
+// K3: piece finalize (one CTA per tile, one piece per thread).  Size additions into
+// the same cluster root are combined per warp first, because the percolating
+// cluster collects pieces from most tiles.
 // --------------------------------------------------------------------------------------
 template <int NL>
 __global__ void __launch_bounds__(256)
-k_piece_finalize(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
-    const int64_t t = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (t >= ntiles) return;
+k_piece_finalize(const __grid_constant__ LatBatch<NL> B, Work W) {
+    const int64_t t = blockIdx.x;
     const int lane = threadIdx.x & 31;
     const int4 ti = W.tinfo[t];
     if (ti.y == 0) return;
     const LatDev &L = B.lat[(NL == 1) ? 0 : find_lattice(B.lat, B.n, t)];
-    for (int j0 = 0; j0 < ti.y; j0 += 32) {
+    for (int j0 = (threadIdx.x & ~31); j0 < ti.y; j0 += 256) {
         const int j = j0 + lane;
         const bool valid = j < ti.y;
         const int pid = ti.x + j;
@@ -767,7 +828,7 @@ static cudaError_t launch_all(const LatDev *lats, int n, const Plan &P, const Wo
     mark(2);
     k_face_merge<TY, TZ, NL><<<(unsigned)P.ntiles, SH::NT, 0, st>>>(B, W);
     mark(3);
-    k_piece_finalize<NL><<<(unsigned)((P.ntiles + 7) / 8), 256, 0, st>>>(B, W, P.ntiles);
+    k_piece_finalize<NL><<<(unsigned)P.ntiles, 256, 0, st>>>(B, W);
     mark(4);
     const int64_t nb = (P.nseg + SCAN_CH) / SCAN_CH;   // covers index nseg (the total)
     k_scan_reduce<<<(unsigned)nb, SCAN_NT, 0, st>>>(W.cnt, P.nseg, W.bsum);

@@ -33,7 +33,7 @@ void *g_scratch_addr[MAX_DEVICES];
 size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct Carve {
-    size_t mask, codes, cnt, pre, bsum, face, tinfo, parent, key, psize, status, ncl, total;
+    size_t mask, codes, cnt, pre, bsum, face, tinfo, parent, key, psize, xcol, status, ncl, total;
 };
 
 Carve carve(const hk::TileInfo &ti, const hk::Plan &P) {
@@ -51,6 +51,7 @@ Carve carve(const hk::TileInfo &ti, const hk::Plan &P) {
     c.parent = take((size_t)P.piece_cap * 4);
     c.key = take((size_t)P.piece_cap * 4);
     c.psize = take((size_t)P.piece_cap * 4);
+    c.xcol = take((size_t)P.ntiles * (ti.rows / 32) * 2 * 4);
     c.status = take(4);
     c.ncl = take(8);
     c.total = off;
@@ -101,6 +102,7 @@ extern "C" int hk_label_noalloc(const float *phi, int nx, int ny, int nz, const 
     W.parent = reinterpret_cast<int32_t *>(base + c.parent);
     W.key = reinterpret_cast<int32_t *>(base + c.key);
     W.psize = reinterpret_cast<int32_t *>(base + c.psize);
+    W.xcol = reinterpret_cast<uint32_t *>(base + c.xcol);
     W.status = reinterpret_cast<int32_t *>(base + c.status);
     W.piece_cap = P.piece_cap;
 
