@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--tile", default="", help="ty,tz tile override")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="headline config only")
+    ap.add_argument("--served-requests", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -154,6 +156,120 @@ def run_reference(args, rank, world):
             "cpu_baseline": {"value": value, "unit": "Gsites/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "Gsites/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def flush_l2(buf):
+    buf.add_(1)   # rewrites a buffer larger than L2
+
+
+def time_single(lab, phi, per, reps, flush=None):
+    """Median device time (ms) of hk_label on a resident lattice, L2 flushed between reps."""
+    import torch
+    out = lab.alloc_outputs(phi.shape, phi.device)
+    s = torch.cuda.current_stream()
+    for _ in range(3):
+        lab.label(phi, per, out=out)
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush_l2(flush)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        lab.label(phi, per, out=out)
+        b.record(s)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts)), int(out[3].item())
+
+
+def extra_configs(args, peak):
+    """The other four workloads: 32^3, 256^3 emulsion, the uneven batch, the served stream."""
+    import torch
+    from paper_1405_1931_gb300 import autotune, fields, hk, serve
+    res = {}
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    lab = hk.Labeller(0)
+
+    def line(name, n_sites, ms, ncl, workload, cache):
+        b = 8 * n_sites + 8 * ncl + 256
+        res[name] = {"workload": workload, "gsites_per_s": n_sites / (ms * 1e-3) / 1e9, "ms": ms,
+                     "n_clusters": ncl, "roofline_frac": b / (ms * 1e-3) / 1e9 / peak, "cache": cache}
+
+    # 32^3, occupancy 0.3, seed 0
+    phi = torch.empty((32, 32, 32), dtype=torch.float32, device="cuda")
+    hk.hk_gen_iid(phi.data_ptr(), 32, 32, 32, 0, 0.3, hk._stream_handle(None))
+    ms, ncl = time_single(lab, phi, (1, 1, 1), 50, flush)
+    line("small32", 32 ** 3, ms, ncl, "32^3 iid p=0.3 periodic xyz", "L2 flushed between reps")
+    # 256^3 emulsion, 600 droplets r in [5, 15]
+    L = 256
+    phi = torch.empty((L, L, L), dtype=torch.float32, device="cuda")
+    c, r = fields.sphere_params(600, (L, L, L), seed=1)
+    hk.hk_gen_spheres(phi.data_ptr(), L, L, L, c, r, 8.0, hk._stream_handle(None))
+    ms, ncl = time_single(lab, phi, (1, 1, 1), 20, flush)
+    line("emulsion256", L ** 3, ms, ncl, "256^3 emulsion, 600 droplets r in [5,15], periodic", "L2 flushed between reps")
+    del phi
+
+    # uneven batch of 96 lattices: per-lattice launches vs one batched launch sequence
+    params = fields.batch_params(96, master_seed=2)
+    s = torch.cuda.Stream()
+    items = []
+    with torch.cuda.stream(s):
+        for prm in params:
+            d = torch.empty((prm["nz"], prm["ny"], prm["nx"]), dtype=torch.float32, device="cuda")
+            hk.hk_gen_iid(d.data_ptr(), prm["nx"], prm["ny"], prm["nz"], prm["seed"], prm["occupancy"],
+                          hk._stream_handle(s))
+            items.append((d, prm["periodic"], lab.alloc_outputs(d.shape, d.device)))
+    s.synchronize()
+    sites = sum(int(d.numel()) for d, _, _ in items)
+    tuned = autotune.tune(lab, items, stream=s, reps=2, cache=None)
+
+    def timed(fn, reps=5):
+        with torch.cuda.stream(s):
+            fn()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            for _ in range(reps):
+                fn()
+            b.record(s)
+        b.synchronize()
+        return a.elapsed_time(b) / reps
+
+    per = timed(lambda: [lab.label(d, p_, out=o, stream=s) for d, p_, o in items])
+    bat = timed(lambda: lab.label_batched(items, stream=s))
+    lab.set_graphs(True)
+    gra = timed(lambda: lab.label_batched(items, stream=s))
+    lab.set_graphs(False)
+    lab.set_tile(16, 16)
+    res["batched96"] = {"workload": "96 lattices, axes in {32,...,384}, p in U[0.15,0.45], random periodic flags",
+                        "sites": sites, "tile": list(tuned["tile"]), "autotune_ms": tuned["ms"],
+                        "per_lattice_ms": per, "batched_ms": bat, "batched_graph_ms": gra,
+                        "per_lattice_gsites_per_s": sites / (per * 1e-3) / 1e9,
+                        "batched_gsites_per_s": sites / (bat * 1e-3) / 1e9,
+                        "batched_graph_gsites_per_s": sites / (gra * 1e-3) / 1e9}
+    del items
+    lab.close()
+    torch.cuda.empty_cache()
+
+    # served: Poisson stream, continuous batching vs one launch per request
+    reqs = serve.request_stream(args.served_requests, rate=400.0, seed=3)
+    srv = serve.Server(0, cap_bytes=32 * serve.GB, workers=4)
+    cont = srv.serve(reqs)
+    reqs = serve.request_stream(args.served_requests, rate=400.0, seed=3)
+    fifo = srv.serve(reqs, mode="fifo")
+    # saturated: the same mix arriving far faster than it can be served
+    nsat = max(100, args.served_requests // 4)
+    sat_c = srv.serve(serve.request_stream(nsat, rate=20000.0, seed=4))
+    sat_f = srv.serve(serve.request_stream(nsat, rate=20000.0, seed=4), mode="fifo")
+    srv.close()
+    for st in (cont, fifo, sat_c, sat_f):
+        st.pop("done", None)
+    res["served"] = {"workload": f"{args.served_requests} Poisson requests at 400/s, 80% emulsion / 20% capsule, "
+                                 "side log-uniform in [64,512], 32 GB admission cap",
+                     "continuous": cont, "fifo": fifo,
+                     "saturated": {"workload": f"{nsat} requests of the same mix at 20000/s",
+                                   "continuous": sat_c, "fifo": sat_f}}
+    torch.cuda.empty_cache()
+    return res
 
 
 def main():
@@ -277,6 +393,12 @@ def main():
                "entry": "hk_label_host (pinned host buffers)"}
         del phi_h, lab_h, sizes_h
 
+    extra = None
+    if rank == 0 and not args.no_extra:
+        del out, phi, labels, sizes, hist, ncl
+        torch.cuda.empty_cache()
+        extra = extra_configs(args, peak)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline_oracle()
@@ -291,7 +413,7 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "n_clusters": n_clusters,
                 "passes_ms": dict(zip(names, passes)),
-                "roofline": roofline, "kernels": kernels,
+                "roofline": roofline, "kernels": kernels, "configs": extra,
                 "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": LAUNCHES_PER_CALL * args.steps, "clocks": clk}
         print(json.dumps(line), flush=True)

@@ -121,6 +121,18 @@ typedef struct hk_lattice {
  * HK_ERR_CUDA, HK_ERR_CAPACITY (some lattice overflowed its sizes_cap). */
 int hk_label_batched(hk_ctx *ctx, const hk_lattice *lats, int n, void *stream);
 
+/* Replay batched calls from CUDA graphs.  When enabled, hk_label_batched on a
+ * non-default stream, with timing off and every sizes_cap >= ceil(N/2), keeps
+ * an instantiated CUDA graph of its launch sequence keyed by the exact
+ * descriptors (pointers, shapes, periodic flags, capacities) and the tile
+ * shape; a later call with the same descriptors replays it (one graph launch
+ * instead of one launch per pass).  The first call with new descriptors runs
+ * normally and then captures.  Graphs are dropped when the workspace grows,
+ * when graphs are disabled and by hk_destroy; at most 8 are kept.  Buffers
+ * named by a kept graph must stay allocated while it may be replayed.
+ * Errors: HK_ERR_ARG. */
+int hk_set_graphs(hk_ctx *ctx, int enable);
+
 /* hk_label on HOST buffers: copies phi host->device, labels on the device and
  * copies labels, sizes, hist and the count back; synchronous.  Host buffers
  * may be pageable or pinned (pinned is faster).  Same argument meaning as

@@ -34,6 +34,15 @@ struct hk_ctx {
     int64_t nacc = 0;          // calls already folded into acc
     double acc[hk::NUM_PASSES] = {};
     cudaEvent_t ev[RING][hk::NUM_PASSES + 1] = {};
+    // CUDA graphs of batched calls, keyed by the exact descriptors and tile shape
+    struct GraphEntry {
+        std::vector<hk_lattice> key;
+        int ty, tz;
+        cudaGraphExec_t exec;
+    };
+    static constexpr int MAX_GRAPHS = 8;
+    bool graphs = false;
+    std::vector<GraphEntry> gcache;
 };
 
 namespace {
@@ -81,8 +90,14 @@ int fail_cuda(hk_ctx *ctx, cudaError_t e) {
     return HK_ERR_CUDA;
 }
 
+void drop_graphs(hk_ctx *ctx) {
+    for (auto &g : ctx->gcache) cudaGraphExecDestroy(g.exec);
+    ctx->gcache.clear();
+}
+
 int ensure_ws(hk_ctx *ctx, size_t bytes) {
     if (bytes <= ctx->ws_bytes) return HK_OK;
+    drop_graphs(ctx);   // captured graphs point into the old workspace
     if (ctx->ws) {
         cudaDeviceSynchronize();
         cudaFree(ctx->ws);
@@ -331,6 +346,7 @@ void hk_destroy(hk_ctx *ctx) {
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->io) cudaFree(ctx->io);
     if (ctx->dstatus) cudaFree(ctx->dstatus);
+    drop_graphs(ctx);
     for (auto &set : ctx->ev)
         for (auto &e : set)
             if (e) cudaEventDestroy(e);
@@ -372,7 +388,61 @@ int hk_label(hk_ctx *ctx, const float *phi, int nx, int ny, int nz, const int pe
 int hk_label_batched(hk_ctx *ctx, const hk_lattice *lats, int n, void *stream) {
     if (!ctx || n < 0 || (n > 0 && !lats)) return HK_ERR_ARG;
     if (n == 0) return HK_OK;
-    return run_lattices(ctx, lats, n, static_cast<cudaStream_t>(stream));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    bool graphable = ctx->graphs && st != nullptr && !ctx->timing;
+    for (int i = 0; i < n && graphable; ++i) {
+        const int64_t N = (int64_t)lats[i].nx * lats[i].ny * lats[i].nz;
+        if (check_lattice(lats[i]) != HK_OK || lats[i].sizes_cap < (N + 1) / 2) graphable = false;
+    }
+    if (!graphable) return run_lattices(ctx, lats, n, st);
+
+    auto same = [&](const std::vector<hk_lattice> &key) {
+        if ((int)key.size() != n) return false;
+        for (int i = 0; i < n; ++i) {
+            const hk_lattice &a = key[i], &b = lats[i];
+            if (a.phi != b.phi || a.nx != b.nx || a.ny != b.ny || a.nz != b.nz || a.labels != b.labels ||
+                a.sizes != b.sizes || a.sizes_cap != b.sizes_cap || a.hist != b.hist || a.n_clusters != b.n_clusters ||
+                (a.periodic[0] != 0) != (b.periodic[0] != 0) || (a.periodic[1] != 0) != (b.periodic[1] != 0) ||
+                (a.periodic[2] != 0) != (b.periodic[2] != 0))
+                return false;
+        }
+        return true;
+    };
+    for (auto &g : ctx->gcache)
+        if (g.ty == ctx->ty && g.tz == ctx->tz && same(g.key))
+            return cudaGraphLaunch(g.exec, st) == cudaSuccess ? HK_OK : fail_cuda(ctx, cudaGetLastError());
+
+    // First call with these descriptors: run once uncaptured (sizes the workspace,
+    // sets kernel attributes), then capture the same launch sequence and keep it.
+    int rc = run_lattices(ctx, lats, n, st);
+    if (rc != HK_OK) return rc;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return fail_cuda(ctx, e);
+    rc = run_lattices(ctx, lats, n, st);
+    e = cudaStreamEndCapture(st, &graph);
+    if (rc != HK_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return rc != HK_OK ? rc : fail_cuda(ctx, e);
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail_cuda(ctx, e);
+    if ((int)ctx->gcache.size() >= hk_ctx::MAX_GRAPHS) {
+        cudaGraphExecDestroy(ctx->gcache.front().exec);
+        ctx->gcache.erase(ctx->gcache.begin());
+    }
+    ctx->gcache.push_back({std::vector<hk_lattice>(lats, lats + n), ctx->ty, ctx->tz, exec});
+    return HK_OK;   // this call's results came from the uncaptured run
+}
+
+int hk_set_graphs(hk_ctx *ctx, int enable) {
+    if (!ctx) return HK_ERR_ARG;
+    ctx->graphs = enable != 0;
+    if (!ctx->graphs) drop_graphs(ctx);
+    return HK_OK;
 }
 
 int hk_label_host(hk_ctx *ctx, const float *phi_host, int nx, int ny, int nz, const int periodic[3],

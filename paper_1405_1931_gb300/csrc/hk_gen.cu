@@ -125,8 +125,8 @@ int hk_gen_spheres(float *phi, int nx, int ny, int nz, const double *centres_xyz
     if (cudaMemcpyAsync(d, h.data(), sizeof(Sphere) * n_spheres, cudaMemcpyHostToDevice, st) != cudaSuccess) return 4;
     k_gen_spheres<<<n_spheres, 256, 0, st>>>(phi, nx, ny, nz, d, (float)reach);
     cudaFreeAsync(d, st);
-    // the pageable source of the copy above must stay valid until the copy ran
-    if (cudaStreamSynchronize(st) != cudaSuccess) return 4;
+    // a copy from pageable memory is staged before cudaMemcpyAsync returns, so the
+    // host vector may go out of scope here
     return cudaGetLastError() == cudaSuccess ? 0 : 4;
 }
 

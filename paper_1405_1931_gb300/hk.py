@@ -20,7 +20,7 @@ HK_OK, HK_ERR_ARG, HK_ERR_TOO_LARGE, HK_ERR_CAPACITY = 0, 1, 2, 3
 HK_ERR_CUDA, HK_ERR_TIMEOUT, HK_ERR_NOMEM = 4, 5, 6
 
 EXPORTED = ("hk_create", "hk_destroy", "hk_workspace_bytes", "hk_reserve", "hk_label", "hk_label_batched",
-            "hk_label_host", "hk_set_tile", "hk_set_timing", "hk_get_timing", "hk_sync_status", "hk_last_cuda_error", "hk_strerror", "hk_label_noalloc",
+            "hk_label_host", "hk_set_tile", "hk_set_timing", "hk_get_timing", "hk_sync_status", "hk_set_graphs", "hk_last_cuda_error", "hk_strerror", "hk_label_noalloc",
             "hk_gen_iid", "hk_gen_spheres", "hk_gen_capsule")
 
 _lock = threading.Lock()
@@ -64,6 +64,7 @@ def load():
             "hk_label_noalloc": (I, [P, I, I, I, P, P, P, I64, P, P, P]),
             "hk_set_tile": (I, [P, I, I]),
             "hk_set_timing": (I, [P, I]),
+            "hk_set_graphs": (I, [P, I]),
             "hk_get_timing": (I, [P, ctypes.POINTER(ctypes.c_float), I, ctypes.POINTER(ctypes.c_int)]),
             "hk_sync_status": (I, [P, P]),
             "hk_last_cuda_error": (I, [P]),
@@ -153,6 +154,10 @@ def hk_get_timing(ctx):
     return [float(buf[i]) for i in range(n.value)]
 
 
+def hk_set_graphs(ctx, enable: bool) -> int:
+    return load().hk_set_graphs(ctx, int(bool(enable)))
+
+
 def hk_sync_status(ctx, stream=0) -> int:
     return load().hk_sync_status(ctx, stream)
 
@@ -219,6 +224,11 @@ class Labeller:
         if rc != HK_OK:
             raise HKError(rc, "hk_set_tile")
         self.tile = (ty, tz)
+
+    def set_graphs(self, enable: bool = True):
+        rc = hk_set_graphs(self.ctx, enable)
+        if rc != HK_OK:
+            raise HKError(rc, "hk_set_graphs")
 
     def sync_status(self, stream=None):
         """Synchronise and raise if a bounded device-side loop gave up since the last check."""
