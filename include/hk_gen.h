@@ -32,6 +32,12 @@ int hk_gen_iid(float *phi, int nx, int ny, int nz, uint64_t seed, double occupan
 int hk_gen_spheres(float *phi, int nx, int ny, int nz, const double *centres_xyz, const double *radii,
                    int n_spheres, double reach, void *stream);
 
+/* As hk_gen_spheres, with the spheres already on the device: `spheres` is a
+ * device array of n_spheres x 4 floats (cx, cy, cz, r).  Launches only; the
+ * host does not wait. */
+int hk_gen_spheres_dev(float *phi, int nx, int ny, int nz, const float *spheres, int n_spheres, double reach,
+                       void *stream);
+
 /* Closed ellipsoidal shell in an L^3 box: phi = -1 where F <= 1 and some
  * 6-neighbour has F > 1, else +1; F = sum_i ((x_i - L/2) / a_i)^2 evaluated in
  * float64 without contraction, identical to the host generator. */

@@ -130,6 +130,18 @@ int hk_gen_spheres(float *phi, int nx, int ny, int nz, const double *centres_xyz
     return cudaGetLastError() == cudaSuccess ? 0 : 4;
 }
 
+int hk_gen_spheres_dev(float *phi, int nx, int ny, int nz, const float *spheres, int n_spheres, double reach,
+                       void *stream) {
+    if (!phi || nx < 1 || ny < 1 || nz < 1 || n_spheres < 0 || (n_spheres > 0 && !spheres)) return 1;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t n = (int64_t)nx * ny * nz;
+    k_fill<<<grid_for(n, 1), 256, 0, st>>>(phi, n, -1.0f);
+    if (n_spheres > 0)
+        k_gen_spheres<<<n_spheres, 256, 0, st>>>(phi, nx, ny, nz, reinterpret_cast<const Sphere *>(spheres),
+                                                  (float)reach);
+    return cudaGetLastError() == cudaSuccess ? 0 : 4;
+}
+
 int hk_gen_capsule(float *phi, int L, double ax, double ay, double az, void *stream) {
     if (!phi || L < 1 || ax <= 0 || ay <= 0 || az <= 0) return 1;
     const int64_t n = (int64_t)L * L * L;

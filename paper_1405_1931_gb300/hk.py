@@ -21,7 +21,7 @@ HK_ERR_CUDA, HK_ERR_TIMEOUT, HK_ERR_NOMEM = 4, 5, 6
 
 EXPORTED = ("hk_create", "hk_destroy", "hk_workspace_bytes", "hk_reserve", "hk_label", "hk_label_batched",
             "hk_label_host", "hk_set_tile", "hk_set_timing", "hk_get_timing", "hk_sync_status", "hk_set_graphs", "hk_last_cuda_error", "hk_strerror", "hk_label_noalloc",
-            "hk_gen_iid", "hk_gen_spheres", "hk_gen_capsule")
+            "hk_gen_iid", "hk_gen_spheres", "hk_gen_spheres_dev", "hk_gen_capsule")
 
 _lock = threading.Lock()
 _lib = None
@@ -72,6 +72,7 @@ def load():
             "hk_gen_iid": (I, [P, I, I, I, ctypes.c_uint64, ctypes.c_double, P]),
             "hk_gen_spheres": (I, [P, I, I, I, P, P, I, ctypes.c_double, P]),
             "hk_gen_capsule": (I, [P, I, ctypes.c_double, ctypes.c_double, ctypes.c_double, P]),
+            "hk_gen_spheres_dev": (I, [P, I, I, I, P, I, ctypes.c_double, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -178,6 +179,10 @@ def hk_gen_spheres(phi, nx, ny, nz, centres, radii, reach=8.0, stream=0) -> int:
     c = np.ascontiguousarray(centres, dtype=np.float64).reshape(-1)
     r = np.ascontiguousarray(radii, dtype=np.float64).reshape(-1)
     return load().hk_gen_spheres(phi, nx, ny, nz, c.ctypes.data, r.ctypes.data, int(r.size), float(reach), stream)
+
+
+def hk_gen_spheres_dev(phi, nx, ny, nz, spheres_dev, n_spheres, reach=8.0, stream=0) -> int:
+    return load().hk_gen_spheres_dev(phi, nx, ny, nz, spheres_dev, int(n_spheres), float(reach), stream)
 
 
 def hk_gen_capsule(phi, L, ax, ay, az, stream=0) -> int:

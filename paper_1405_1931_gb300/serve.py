@@ -14,8 +14,10 @@ buffers resident on the device and:
   batch as soon as a worker frees up;
 * detects completion with CUDA events and frees the request's memory.
 
-Latency is measured per request from its arrival to the host observing its
-completion event.  ``mode="fifo"`` serves the same stream with one
+Latency is reported two ways: from the request's arrival to the host
+observing its completion event, and from its field being ready on the device
+to its labels being ready (CUDA events: queueing plus labelling, without the
+stand-in simulation's generation time).  ``mode="fifo"`` serves the same stream with one
 ``hk_label`` launch per request in arrival order on one stream (one worker),
 as the baseline.  Results are bit-identical between the modes and to labelling each
 request alone (the tests check this).
@@ -47,6 +49,8 @@ class Request:
     phi: object = None
     out: object = None
     gen_event: object = None
+    sphere_ptr: int = 0
+    ready_to_done_ms: float = math.nan
     t_done: float = math.nan
     n_clusters: int = -1
 
@@ -89,13 +93,37 @@ def request_stream(n: int = 2000, rate: float = 400.0, seed: int = 3, frac_emuls
     return out
 
 
+def upload_spheres(requests: list):
+    """Put every emulsion request's droplets on the device once (the simulation's state).
+
+    Returns the device tensor; each request gets `sphere_ptr` into it (4 floats a droplet).
+    """
+    import torch
+    chunks, offs, total = [], [], 0
+    for r in requests:
+        if r.kind == "emulsion":
+            c, rad = r.spheres
+            a = np.concatenate([c, rad[:, None]], axis=1).astype(np.float32).reshape(-1)
+            offs.append((r, total))
+            chunks.append(a)
+            total += a.size
+    host = torch.from_numpy(np.concatenate(chunks) if chunks else np.zeros(4, np.float32)).pin_memory()
+    dev = host.to("cuda", non_blocking=True)
+    torch.cuda.current_stream().synchronize()
+    for r, off in offs:
+        r.sphere_ptr = dev.data_ptr() + 4 * off
+    return dev
+
+
 def generate(req: Request, stream) -> None:
     """Write the request's phi on the device (the simulation stand-in)."""
     import torch
     L = req.L
     req.phi = torch.empty((L, L, L), dtype=torch.float32, device="cuda")
     h = hk._stream_handle(stream)
-    if req.kind == "emulsion":
+    if req.kind == "emulsion" and getattr(req, "sphere_ptr", None):
+        rc = hk.hk_gen_spheres_dev(req.phi.data_ptr(), L, L, L, req.sphere_ptr, len(req.spheres[1]), 8.0, h)
+    elif req.kind == "emulsion":
         centres, radii = req.spheres
         rc = hk.hk_gen_spheres(req.phi.data_ptr(), L, L, L, centres, radii, 8.0, h)
     else:
@@ -106,12 +134,14 @@ def generate(req: Request, stream) -> None:
 
 class Server:
     def __init__(self, device: int = 0, cap_bytes: int = 32 * GB, workers: int = 4, max_batch: int = 64,
-                 tile: tuple | None = None, graphs: bool = False):
+                 max_batch_sites: int = 1 << 28, tile: tuple | None = None, graphs: bool = False,
+                 producers: int = 4):
         import torch
         self.device = device
         self.cap = cap_bytes
         self.max_batch = max_batch
-        self.producer = torch.cuda.Stream(device=device)
+        self.max_batch_sites = max_batch_sites   # bounds each worker's workspace
+        self.producers = [torch.cuda.Stream(device=device) for _ in range(producers)]
         self.streams = [torch.cuda.Stream(device=device) for _ in range(workers)]
         self.labs = [hk.Labeller(device, tile=tile) for _ in range(workers)]
         for lab in self.labs:
@@ -125,12 +155,14 @@ class Server:
     def serve(self, requests: list, mode: str = "continuous", keep_outputs: bool = False) -> dict:
         """Serve `requests` (arrival times in seconds from now) and return statistics."""
         import torch
+        spheres_dev = upload_spheres(requests)   # noqa: F841  (kept alive for the run)
         pending = deque(sorted(requests, key=lambda r: r.arrival))
         ready = deque()          # admitted, field generation issued, not yet launched
         inflight = []            # (worker, [requests], end_event)
         # continuous batching uses every worker; the baseline is one launch per
         # request, in arrival order, on a single stream
-        free = list(range(len(self.streams))) if mode != "fifo" else [0]
+        fifo = mode == "fifo"
+        free = list(range(len(self.streams)))
         used = 0
         peak_used = 0
         done = []
@@ -145,13 +177,15 @@ class Server:
                     tdone = time.perf_counter() - t0
                     for r in batch:
                         r.t_done = tdone
+                        r.ready_to_done_ms = r.gen_event.elapsed_time(ev)
                         r.n_clusters = int(r.out[3].item()) if keep_outputs else -1
                         used -= r.nbytes()
                         if not keep_outputs:
                             r.phi = None
                             r.out = None
                         done.append(r)
-                    free.append(w)
+                    if not fifo:
+                        free.append(w)
                 else:
                     still.append((w, batch, ev))
             inflight = still
@@ -160,20 +194,26 @@ class Server:
                 r = pending.popleft()
                 used += r.nbytes()
                 peak_used = max(peak_used, used)
-                with torch.cuda.stream(self.producer):
-                    generate(r, self.producer)
+                prod = self.producers[r.rid % len(self.producers)]
+                with torch.cuda.stream(prod):
+                    generate(r, prod)
                     r.out = hk.Labeller.alloc_outputs(r.phi.shape, r.phi.device)
-                    r.gen_event = torch.cuda.Event()
-                    r.gen_event.record(self.producer)
+                    r.gen_event = torch.cuda.Event(enable_timing=True)
+                    r.gen_event.record(prod)
                 ready.append(r)
             # 3. launches
-            if ready and free:
-                w = free.pop(0)
+            if ready and (free or fifo):
+                # fifo: every request is its own launch, enqueued back to back on stream 0
+                w = 0 if fifo else free.pop(0)
                 s = self.streams[w]
-                if mode == "fifo":
+                if fifo:
                     batch = [ready.popleft()]
                 else:
-                    batch = [ready.popleft() for _ in range(min(self.max_batch, len(ready)))]
+                    batch = [ready.popleft()]
+                    sites = batch[0].sites
+                    while ready and len(batch) < self.max_batch and sites + ready[0].sites <= self.max_batch_sites:
+                        sites += ready[0].sites
+                        batch.append(ready.popleft())
                 for r in batch:
                     s.wait_event(r.gen_event)
                 with torch.cuda.stream(s):
@@ -182,7 +222,7 @@ class Server:
                         self.labs[w].label(r.phi, r.periodic, out=r.out, stream=s)
                     else:
                         self.labs[w].label_batched([(r.phi, r.periodic, r.out) for r in batch], stream=s)
-                    ev = torch.cuda.Event()
+                    ev = torch.cuda.Event(enable_timing=True)
                     ev.record(s)
                 busy_sites += sum(r.sites for r in batch)
                 inflight.append((w, batch, ev))
@@ -193,11 +233,13 @@ class Server:
                     time.sleep(min(wait, 0.001))
         wall = max(r.t_done for r in done) if done else 0.0
         lat = np.array([r.t_done - r.arrival for r in done]) * 1e3
+        lat_ready = np.array([r.ready_to_done_ms for r in done])
         sites = sum(r.sites for r in done)
         return {"mode": mode, "requests": len(done), "wall_s": wall, "sites": sites,
                 "gsites_per_s": sites / wall / 1e9 if wall > 0 else 0.0,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+                "ready_p50_ms": float(np.percentile(lat_ready, 50)), "ready_p99_ms": float(np.percentile(lat_ready, 99)),
                 "peak_admitted_gb": peak_used / GB, "cap_gb": self.cap / GB,
-                "workers": len(self.streams) if mode != "fifo" else 1,
+                "workers": 1 if fifo else len(self.streams),
                 "done": done}
