@@ -160,6 +160,9 @@ struct LabelSmem {
     uint32_t nzlo[TY], nzhi[TY];           // neighbour rows across the z faces, per row
     uint32_t nxlo[SH::R / 32], nxhi[SH::R / 32];   // neighbour columns across the x faces
     static_assert(TZ <= 16 && TY <= 32 && SH::R / 32 <= 16 && SH::NT >= 64, "face loads use threads 0..63");
+    uint32_t chunkbal[SH::MAXRUNS / 32];   // boundary-root ballot of each chunk of 32 run ids
+    int chunkpre[SH::MAXRUNS / 32];        // boundary roots before each chunk
+    int nb;
     int warp_tmp[32];
 };
 
@@ -230,51 +233,46 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
         S.rbase[r] = rb;
         for (int i = r; i < total; i += NT) S.par[i] = i;
 
-        // y-neighbours: one union per overlapping run pair of rows (y-1, y)
+        // y- and z-neighbours: one union per overlapping run pair of rows (y-1, y) and
+        // (z-1, z).  Both pair lists come from one scan of packed counts (each total
+        // is at most 16 * R < 2^16) and normally share one pass of unions.
         const uint32_t osy = ly > 0 ? run_starts(m & S.m[r - 1]) : 0u;
-        int ny_tot;
-        const int yb = block_exscan<NT>(__popc(osy), S.warp_tmp, ny_tot);
-        if (osy) {
-            const uint32_t mq = S.m[r - 1];
-            const uint32_t rsq = run_starts(mq);
-            const int rbq = S.rbase[r - 1];
-            uint32_t w = osy;
-            int j = yb;
-            while (w) {
-                const int x = __ffs(w) - 1;
-                w &= w - 1;
-                S.aux[j++] = (run_of(rb, rs, x) << 16) | run_of(rbq, rsq, x);
-            }
-        }
-        __syncthreads();
-        for (int i = tid; i < ny_tot; i += NT) {
-            const uint32_t p = (uint32_t)S.aux[i];
-            s_union(S.par, (int)(p >> 16), (int)(p & 0xffffu), total, W.status);
-        }
-        __syncthreads();
-
-        // z-neighbours
         const uint32_t osz = lz > 0 ? run_starts(m & S.m[r - TY]) : 0u;
-        int nz_tot;
-        const int zb = block_exscan<NT>(__popc(osz), S.warp_tmp, nz_tot);
-        if (osz) {
-            const uint32_t mq = S.m[r - TY];
+        int tot_packed;
+        const int packed = block_exscan<NT>(__popc(osy) | (__popc(osz) << 16), S.warp_tmp, tot_packed);
+        const int ny_tot = tot_packed & 0xffff, nz_tot = tot_packed >> 16;
+        auto write_pairs = [&](uint32_t os, int q, int j) {
+            const uint32_t mq = S.m[q];
             const uint32_t rsq = run_starts(mq);
-            const int rbq = S.rbase[r - TY];
-            uint32_t w = osz;
-            int j = zb;
-            while (w) {
-                const int x = __ffs(w) - 1;
-                w &= w - 1;
+            const int rbq = S.rbase[q];
+            while (os) {
+                const int x = __ffs(os) - 1;
+                os &= os - 1;
                 S.aux[j++] = (run_of(rb, rs, x) << 16) | run_of(rbq, rsq, x);
             }
+        };
+        auto union_pairs = [&](int n) {
+            for (int i = tid; i < n; i += NT) {
+                const uint32_t p = (uint32_t)S.aux[i];
+                s_union(S.par, (int)(p >> 16), (int)(p & 0xffffu), total, W.status);
+            }
+        };
+        if (ny_tot + nz_tot <= MR) {            // block-uniform
+            if (osy) write_pairs(osy, r - 1, packed & 0xffff);
+            if (osz) write_pairs(osz, r - TY, ny_tot + (packed >> 16));
+            __syncthreads();
+            union_pairs(ny_tot + nz_tot);
+            __syncthreads();
+        } else {
+            if (osy) write_pairs(osy, r - 1, packed & 0xffff);
+            __syncthreads();
+            union_pairs(ny_tot);
+            __syncthreads();
+            if (osz) write_pairs(osz, r - TY, packed >> 16);
+            __syncthreads();
+            union_pairs(nz_tot);
+            __syncthreads();
         }
-        __syncthreads();
-        for (int i = tid; i < nz_tot; i += NT) {
-            const uint32_t p = (uint32_t)S.aux[i];
-            s_union(S.par, (int)(p >> 16), (int)(p & 0xffffu), total, W.status);
-        }
-        __syncthreads();
 
         // periodic edges inside the tile (an axis that fits in one tile)
         if (g.wrapX || g.wrapY || g.wrapZ) {
@@ -333,23 +331,34 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
         }
         __syncthreads();
 
-        // number the boundary roots in run order; par[root] = -1 - k marks them
-        const int per = (total + NT - 1) / NT;
-        const int i0 = tid * per;
-        int cnt = 0;
-        for (int j = 0; j < per; ++j) {
-            const int i = i0 + j;
-            if (i < total && S.par[i] >= ROOTPOS && S.aux[i] >= AUX_FACE) ++cnt;
-        }
-        int nb;
-        int k = block_exscan<NT>(cnt, S.warp_tmp, nb);
-        for (int j = 0; j < per; ++j) {
-            const int i = i0 + j;
-            if (i < total && S.par[i] >= ROOTPOS && S.aux[i] >= AUX_FACE) S.par[i] = -1 - (k++);
+        // number the boundary roots in run order; par[root] = -1 - k marks them.
+        // Lanes take consecutive run ids (conflict-free); chunks of 32 ids are counted
+        // by ballot and scanned.
+        {
+            const int lane = tid & 31, wid = tid >> 5;
+            constexpr int NW = NT / 32;
+            const int nchunks = (total + 31) / 32;
+            for (int c = wid; c < nchunks; c += NW) {
+                const int i = c * 32 + lane;
+                const bool f = i < total && S.par[i] >= ROOTPOS && S.aux[i] >= AUX_FACE;
+                const uint32_t bal = __ballot_sync(0xffffffffu, f);
+                if (lane == 0) S.chunkbal[c] = bal;
+            }
+            __syncthreads();
+            int nb_;
+            const int cpre = block_exscan<NT>(tid < nchunks ? __popc(S.chunkbal[tid]) : 0, S.warp_tmp, nb_);
+            if (tid < nchunks) S.chunkpre[tid] = cpre;
+            __syncthreads();
+            for (int c = wid; c < nchunks; c += NW) {
+                const uint32_t bal = S.chunkbal[c];
+                if ((bal >> lane) & 1u) S.par[c * 32 + lane] = -1 - (S.chunkpre[c] + __popc(bal & ((1u << lane) - 1u)));
+            }
+            if (tid == 0) S.nb = nb_;
         }
         const int base = (int)(t * SH::MAX_BOUNDARY);   // fixed slice of the piece table
-        if (tid == 0) W.tinfo[t] = make_int4(base, nb, total, 0);
         __syncthreads();
+        const int nb = S.nb;
+        if (tid == 0) W.tinfo[t] = make_int4(base, nb, total, 0);
 
         // boundary pieces into the global table; interior roots counted per row segment
         if (ly <= g.lastY && lz <= g.lastZ) {
