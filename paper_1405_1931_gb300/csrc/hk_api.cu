@@ -53,7 +53,7 @@ constexpr int64_t MAX_SITES = (int64_t)1 << 31;
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t mask, codes, cnt, pre, bsum, face, tinfo, parent, key, psize, xcol, ncl, total;
+    size_t mask, codes, cnt, pre, bsum, face, tinfo, parent, key, psize, xcol, ovf, ncl, total;
 };
 
 Layout make_layout(const TileInfo &ti, const Plan &P) {
@@ -72,6 +72,7 @@ Layout make_layout(const TileInfo &ti, const Plan &P) {
     L.key = take((size_t)P.piece_cap * 4);
     L.psize = take((size_t)P.piece_cap * 4);
     L.xcol = take((size_t)P.ntiles * (ti.rows / 32) * 2 * 4);
+    L.ovf = take((size_t)P.ntiles * 4);
     L.ncl = take((size_t)hk::MAX_LAT_PER_LAUNCH * 8);
     L.total = off;
     return L;
@@ -282,6 +283,8 @@ int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st) {
         W.psize = reinterpret_cast<int32_t *>(base + Ly.psize);
         W.xcol = reinterpret_cast<uint32_t *>(base + Ly.xcol);
         W.status = ctx->dstatus;
+        W.ovf = reinterpret_cast<int32_t *>(base + Ly.ovf);
+        W.novf = ctx->dstatus + 1;
         W.piece_cap = P.piece_cap;
         int64_t *slots = reinterpret_cast<int64_t *>(base + Ly.ncl);
         bool chunk_check = false;

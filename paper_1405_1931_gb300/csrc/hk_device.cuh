@@ -65,6 +65,8 @@ struct Work {
     uint32_t *xcol;     // [ntiles * 2 * R/32] occupancy of each tile's first (x = 0) and last
                         // (x = lastX) column, one bit per tile row
     int32_t *status;    // [1] device-side error flags (STATUS_*), owned by the context
+    int32_t *ovf;       // [ntiles] tiles with more runs than the fast tile pass holds
+    int32_t *novf;      // [1] entries of ovf (reset by the occupancy pass of every call)
     int64_t piece_cap;  // entries of parent/key/psize: bounds every union-find path
 };
 
@@ -89,6 +91,10 @@ struct TileShape {
     static constexpr int R = TY * TZ;            // rows per tile
     static constexpr int SITES = TX * R;
     static constexpr int MAXRUNS = 16 * R;       // at most 16 runs in a 32-site row
+    // Run (and union-pair) capacity of the fast tile pass: 10 runs a row on average,
+    // above the 8 of the densest i.i.d. field (p = 1/2).  Tiles beyond it go to a
+    // second pass sized for MAXRUNS.
+    static constexpr int MR_FAST = 10 * R;
     static constexpr int NT = R;                 // threads per CTA: one per row
     // face layout inside a tile's face block
     static constexpr int OFF_LX = 0;
@@ -211,43 +217,48 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 }
 
 // ---- shared-memory union-find over run ids (union by minimum id) ----------------------
-// par[i] <= i always holds, so a path visits at most `cap` (= number of runs) ids.
-__device__ __forceinline__ int s_find(int *par, int x, int cap, int32_t *status) {
-    volatile int *vp = par;
-    int p = vp[x];
-    for (int it = 0; p != x; ++it) {
-        if (it > cap) { atomicOr(status, STATUS_LOCAL_LOOP); return x; }
-        int gp = vp[p];
-        if (gp == p) return p;
-        vp[x] = gp;          // path halving: gp is an ancestor of x
-        x = gp;
-        p = vp[x];
-    }
-    return x;
-}
+// Every store to par[] lowers it to an ancestor (a root is linked to a smaller id
+// of the other tree, halving stores a grandparent, compression stores the root),
+// so par[i] <= i always holds and a find walks strictly decreasing ids: it ends
+// within i steps by construction.  The union's retry loop is the one that depends
+// on other threads, and it keeps an explicit bound.
 
-// Read-only find for the compression step: without halving stores, no thread
-// can overwrite another thread's final par[i] = root with an older ancestor.
-__device__ __forceinline__ int s_find_ro(const int *par, int x, int cap, int32_t *status) {
+// read-only find: used by compression, where finds run while others store final
+// roots (a halving store there could overwrite a final root with an ancestor)
+__device__ __forceinline__ int s_find_ro(const int *par, int x, int, int32_t *) {
     const volatile int *vp = par;
     int p = vp[x];
-    for (int it = 0; p != x; ++it) {
-        if (it > cap) { atomicOr(status, STATUS_LOCAL_LOOP); return x; }
+    while (p != x) {
         x = p;
         p = vp[x];
     }
     return x;
 }
 
+// find with path halving (during the unions)
+__device__ __forceinline__ int s_find(volatile int *par, int x) {
+    int p = par[x];
+    while (p != x) {
+        const int gp = par[p];
+        if (gp == p) return p;
+        par[x] = gp;
+        x = gp;
+        p = par[x];
+    }
+    return x;
+}
+
 // Each retry strictly lowers max(a, b), so at most `cap` rounds.
 __device__ __forceinline__ void s_union(int *par, int a, int b, int cap, int32_t *status) {
+    volatile int *vp = par;
     for (int it = 0; it <= cap; ++it) {
-        a = s_find(par, a, cap, status);
-        b = s_find(par, b, cap, status);
+        a = s_find(vp, a);
+        b = s_find(vp, b);
         if (a == b) return;
-        if (a > b) { int t = a; a = b; b = t; }
-        int old = atomicMin(&par[b], a);
-        if (old == b) return;
+        const int hi = a > b ? a : b, lo = a > b ? b : a;
+        const int old = atomicMin(&par[hi], lo);
+        if (old == hi) return;
+        a = lo;
         b = old;
     }
     atomicOr(status, STATUS_LOCAL_LOOP);

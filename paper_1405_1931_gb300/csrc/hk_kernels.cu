@@ -30,9 +30,6 @@ struct LatBatch {
 };
 
 // --------------------------------------------------------------------------------------
-// K1: tile labelling
-// --------------------------------------------------------------------------------------
-// --------------------------------------------------------------------------------------
 // K0: occupancy.  One warp per tile streams phi row by row (one coalesced 128-byte
 // load per row, 16 rows in flight per warp) and keeps phi > 0 (Sec. 2) as one
 // 32-bit word per tile row, written tile-major.  Sites outside the lattice count
@@ -44,6 +41,7 @@ __global__ void __launch_bounds__(256) k_occupancy(const __grid_constant__ LatBa
     constexpr int R = SH::R, U = 16;
     const int lane = threadIdx.x & 31;
     const int64_t t = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *W.novf = 0;   // the tile pass appends after this pass
     if (t >= ntiles) return;
     const LatDev &L = B.lat[(NL == 1) ? 0 : find_lattice(B.lat, B.n, t)];
     const TileGeo g = tile_geo<TY, TZ>(L, t);
@@ -98,6 +96,7 @@ __global__ void __launch_bounds__(256) k_occupancy_tma(const __grid_constant__ T
     OccSmem<TY, TZ> &S = *reinterpret_cast<OccSmem<TY, TZ> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const LatDev &L = B.lat[0];
+    if (blockIdx.x == 0 && tid == 0) *W.novf = 0;           // the tile pass appends after this pass
     if (tid == 0) {
         mbar_init(&S.bar[0], 1);
         mbar_init(&S.bar[1], 1);
@@ -147,22 +146,22 @@ __global__ void __launch_bounds__(256) k_occupancy_tma(const __grid_constant__ T
 // --------------------------------------------------------------------------------------
 // K1: tile labelling from the occupancy words (one tile per CTA)
 // --------------------------------------------------------------------------------------
-template <int TY, int TZ>
+template <int TY, int TZ, int CAP>
 struct LabelSmem {
     using SH = TileShape<TY, TZ>;
     uint32_t m[SH::R];                     // occupancy word of each row
     int rbase[SH::R];                      // first run id of each row
-    int par[SH::MAXRUNS];                  // union-find over run ids; see piece_k for the
+    int par[CAP];                          // union-find over run ids; see piece_k for the
                                            // encodings after numbering
-    int aux[SH::MAXRUNS];                  // union pair lists, then per root: size + AUX_FACE * (runs
+    int aux[CAP];                          // union pair lists, then per root: size + AUX_FACE * (runs
                                            // with a site connected across a tile face)
     uint32_t nylo[TZ], nyhi[TZ];           // neighbour rows across the y faces, per plane
     uint32_t nzlo[TY], nzhi[TY];           // neighbour rows across the z faces, per row
     uint32_t nxlo[SH::R / 32], nxhi[SH::R / 32];   // neighbour columns across the x faces
     static_assert(TZ <= 16 && TY <= 32 && SH::R / 32 <= 16 && SH::NT >= 64, "face loads use threads 0..63");
-    uint32_t chunkbal[SH::MAXRUNS / 32];   // boundary-root ballot of each chunk of 32 run ids
-    int chunkpre[SH::MAXRUNS / 32];        // boundary roots before each chunk
-    int nb;
+    uint32_t chunkbal[CAP / 32];           // boundary-root ballot of each chunk of 32 run ids
+    uint32_t chunkint[CAP / 32];           // interior-root ballot of each chunk
+    int chunkpre[CAP / 32];                // boundary roots before each chunk
     int warp_tmp[32];
 };
 
@@ -180,16 +179,30 @@ __device__ __forceinline__ int piece_k(const int *par, int i) {
     return w < 0 ? -1 - w : -1;
 }
 
-template <int TY, int TZ, int NL>
-__global__ void __launch_bounds__(TY * TZ, 1280 / (TY * TZ))
+// Resident CTAs per SM of the fast tile pass (its shared memory and 32 registers a
+// thread allow 2048 threads) and of the pass over the tiles it hands on.
+template <int TY, int TZ, bool FAST>
+struct LabelCfg {
+    static constexpr int CAP = FAST ? TileShape<TY, TZ>::MR_FAST : TileShape<TY, TZ>::MAXRUNS;
+    static constexpr int BLOCKS = FAST ? (2048 / (TY * TZ) < 32 ? 2048 / (TY * TZ) : 32)
+                                       : (1280 / (TY * TZ) < 32 ? 1280 / (TY * TZ) : 32);
+};
+
+// FAST: tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... below ntiles; a tile with
+// more than MR_FAST runs or union pairs of one kind is appended to W.ovf instead.
+// !FAST: the tiles listed in W.ovf, with room for every tile.
+template <int TY, int TZ, int NL, bool FAST>
+__global__ void __launch_bounds__(TY * TZ, (LabelCfg<TY, TZ, FAST>::BLOCKS))
 k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
     using SH = TileShape<TY, TZ>;
-    constexpr int R = SH::R, NT = SH::NT, MR = SH::MAXRUNS;
+    constexpr int R = SH::R, NT = SH::NT, MR = SH::MAXRUNS, CAP = LabelCfg<TY, TZ, FAST>::CAP;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    LabelSmem<TY, TZ> &S = *reinterpret_cast<LabelSmem<TY, TZ> *>(smem_raw);
+    LabelSmem<TY, TZ, CAP> &S = *reinterpret_cast<LabelSmem<TY, TZ, CAP> *>(smem_raw);
     const int tid = threadIdx.x;
+    const int64_t nwork = FAST ? ntiles : (int64_t)*reinterpret_cast<volatile int32_t *>(W.novf);
 
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    for (int64_t it = blockIdx.x; it < nwork; it += gridDim.x) {
+        const int64_t t = FAST ? it : (int64_t)W.ovf[it];
         const LatDev &L = B.lat[(NL == 1) ? 0 : find_lattice(B.lat, B.n, t)];
         const TileGeo g = tile_geo<TY, TZ>(L, t);
 
@@ -229,7 +242,11 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
 
         // a2: run ids (row-major), union lists, unions
         int total;
-        const int rb = block_exscan<NT>(__popc(rs), S.warp_tmp, total);
+        const int rb = block_exscan<NT>(__popc(rs), S.warp_tmp, total);   // ends with a barrier
+        if (FAST && total > CAP) {               // block-uniform; nothing read from S after the scan
+            if (tid == 0) W.ovf[atomicAdd(W.novf, 1)] = (int32_t)t;
+            continue;
+        }
         S.rbase[r] = rb;
         for (int i = r; i < total; i += NT) S.par[i] = i;
 
@@ -241,6 +258,10 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
         int tot_packed;
         const int packed = block_exscan<NT>(__popc(osy) | (__popc(osz) << 16), S.warp_tmp, tot_packed);
         const int ny_tot = tot_packed & 0xffff, nz_tot = tot_packed >> 16;
+        if (FAST && (ny_tot > CAP || nz_tot > CAP)) {   // block-uniform, as above
+            if (tid == 0) W.ovf[atomicAdd(W.novf, 1)] = (int32_t)t;
+            continue;
+        }
         auto write_pairs = [&](uint32_t os, int q, int j) {
             const uint32_t mq = S.m[q];
             const uint32_t rsq = run_starts(mq);
@@ -257,7 +278,7 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
                 s_union(S.par, (int)(p >> 16), (int)(p & 0xffffu), total, W.status);
             }
         };
-        if (ny_tot + nz_tot <= MR) {            // block-uniform
+        if (ny_tot + nz_tot <= CAP) {           // block-uniform
             if (osy) write_pairs(osy, r - 1, packed & 0xffff);
             if (osz) write_pairs(osz, r - TY, ny_tot + (packed >> 16));
             __syncthreads();
@@ -331,18 +352,26 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
         }
         __syncthreads();
 
-        // number the boundary roots in run order; par[root] = -1 - k marks them.
-        // Lanes take consecutive run ids (conflict-free); chunks of 32 ids are counted
-        // by ballot and scanned.
+        // Number the boundary roots in run order (par[root] = -1 - k) and write their
+        // records to the tile's slice of the piece table.  Lanes take consecutive run
+        // ids, so the table stores of a chunk of 32 ids are contiguous; chunks are
+        // counted by ballot and scanned.  Interior roots are kept as a ballot per chunk
+        // for the per-row counts below.
+        const int base = (int)(t * SH::MAX_BOUNDARY);   // fixed slice of the piece table
         {
             const int lane = tid & 31, wid = tid >> 5;
             constexpr int NW = NT / 32;
             const int nchunks = (total + 31) / 32;
             for (int c = wid; c < nchunks; c += NW) {
                 const int i = c * 32 + lane;
-                const bool f = i < total && S.par[i] >= ROOTPOS && S.aux[i] >= AUX_FACE;
-                const uint32_t bal = __ballot_sync(0xffffffffu, f);
-                if (lane == 0) S.chunkbal[c] = bal;
+                const bool root = i < total && S.par[i] >= ROOTPOS;
+                const bool bnd = root && S.aux[i] >= AUX_FACE;
+                const uint32_t bb = __ballot_sync(0xffffffffu, bnd);
+                const uint32_t bi = __ballot_sync(0xffffffffu, root && !bnd);
+                if (lane == 0) {
+                    S.chunkbal[c] = bb;
+                    S.chunkint[c] = bi;
+                }
             }
             __syncthreads();
             int nb_;
@@ -351,34 +380,36 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
             __syncthreads();
             for (int c = wid; c < nchunks; c += NW) {
                 const uint32_t bal = S.chunkbal[c];
-                if ((bal >> lane) & 1u) S.par[c * 32 + lane] = -1 - (S.chunkpre[c] + __popc(bal & ((1u << lane) - 1u)));
-            }
-            if (tid == 0) S.nb = nb_;
-        }
-        const int base = (int)(t * SH::MAX_BOUNDARY);   // fixed slice of the piece table
-        __syncthreads();
-        const int nb = S.nb;
-        if (tid == 0) W.tinfo[t] = make_int4(base, nb, total, 0);
-
-        // boundary pieces into the global table; interior roots counted per row segment
-        if (ly <= g.lastY && lz <= g.lastZ) {
-            uint32_t w = rs;
-            int id = rb;
-            int interior = 0;
-            const int site_row = ((g.z0 + lz) * L.ny + (g.y0 + ly)) * L.nx + g.x0;
-            while (w) {
-                const int x = __ffs(w) - 1;
-                w &= w - 1;
-                const int v = S.par[id];
-                if (v < 0) {
-                    const int pid = base + (-1 - v);
+                if ((bal >> lane) & 1u) {
+                    const int i = c * 32 + lane;
+                    const int k = S.chunkpre[c] + __popc(bal & ((1u << lane) - 1u));
+                    const int pos = S.par[i] & (ROOTPOS - 1);        // row << 5 | x0
+                    const int row = pos >> 5;
+                    const int pid = base + k;
                     W.parent[pid] = pid;
-                    W.key[pid] = site_row + x;
-                    W.psize[pid] = S.aux[id] & (AUX_FACE - 1);
-                } else if (v >= ROOTPOS) {
-                    ++interior;
+                    W.key[pid] = ((g.z0 + row / TY) * L.ny + (g.y0 + row % TY)) * L.nx + g.x0 + (pos & 31);
+                    W.psize[pid] = S.aux[i] & (AUX_FACE - 1);
+                    S.par[i] = -1 - k;
                 }
-                ++id;
+            }
+            if (tid == 0) W.tinfo[t] = make_int4(base, nb_, total, 0);
+        }
+        __syncthreads();
+
+        // interior roots per row segment (a row's runs span at most two chunks)
+        if (ly <= g.lastY && lz <= g.lastZ) {
+            const int n = __popc(rs);
+            int interior = 0;
+            if (n) {
+                const int a = rb, b = rb + n - 1;             // the row's run ids [a, b]
+                const int ca = a >> 5, cb = b >> 5;
+                const uint32_t lo = S.chunkint[ca] >> (a & 31);
+                if (ca == cb) {
+                    interior = __popc(lo & ((1u << n) - 1u));   // n <= 16
+                } else {
+                    const int nh = (b & 31) + 1;                 // ids of the row in chunk cb
+                    interior = __popc(lo) + __popc(S.chunkint[cb] & ((1u << nh) - 1u));
+                }
             }
             const int64_t seg = L.seg0 + ((int64_t)(g.z0 + lz) * L.ny + (g.y0 + ly)) * L.nbx + g.bx;
             W.cnt[seg] = (uint32_t)interior;
@@ -802,12 +833,19 @@ static cudaError_t launch_all(const LatDev *lats, int n, const Plan &P, const Wo
     B.n = n;
     B.pad_ = 0;
     for (int i = 0; i < n; ++i) B.lat[i] = lats[i];
-    const size_t smem1 = sizeof(LabelSmem<TY, TZ>), smem4 = sizeof(FlatSmem<TY, TZ>);
+    constexpr int CAP1 = LabelCfg<TY, TZ, true>::CAP, CAP1B = LabelCfg<TY, TZ, false>::CAP;
+    const size_t smem1 = sizeof(LabelSmem<TY, TZ, CAP1>), smem1b = sizeof(LabelSmem<TY, TZ, CAP1B>);
+    const size_t smem4 = sizeof(FlatSmem<TY, TZ>);
     cudaError_t e;
-    static int grid4 = 0;
+    static int grid4 = 0, grid1b = 0;
     if (!grid4) {
-        e = cudaFuncSetAttribute(k_tile_label<TY, TZ, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
+        e = cudaFuncSetAttribute(k_tile_label<TY, TZ, NL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem1);
         if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_tile_label<TY, TZ, NL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem1b);
+        if (e != cudaSuccess) return e;
+        grid1b = persistent_grid(k_tile_label<TY, TZ, NL, false>, SH::NT, smem1b, INT32_MAX);
         e = cudaFuncSetAttribute(k_flatten<TY, TZ, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4);
         if (e != cudaSuccess) return e;
         grid4 = persistent_grid(k_flatten<TY, TZ, NL>, SH::NT, smem4, INT32_MAX);
@@ -833,7 +871,10 @@ static cudaError_t launch_all(const LatDev *lats, int n, const Plan &P, const Wo
         k_occupancy<TY, TZ, NL><<<(unsigned)((P.ntiles + 7) / 8), 256, 0, st>>>(B, W, P.ntiles);
     }
     mark(1);
-    k_tile_label<TY, TZ, NL><<<(unsigned)P.ntiles, SH::NT, smem1, st>>>(B, W, P.ntiles);
+    k_tile_label<TY, TZ, NL, true><<<(unsigned)P.ntiles, SH::NT, smem1, st>>>(B, W, P.ntiles);
+    // the tiles handed on (none for fields with at most MR_FAST / R runs a row on average)
+    k_tile_label<TY, TZ, NL, false><<<(unsigned)(P.ntiles < grid1b ? P.ntiles : grid1b), SH::NT, smem1b, st>>>(
+        B, W, P.ntiles);
     mark(2);
     k_face_merge<TY, TZ, NL><<<(unsigned)P.ntiles, SH::NT, 0, st>>>(B, W);
     mark(3);

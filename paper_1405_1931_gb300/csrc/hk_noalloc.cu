@@ -33,7 +33,7 @@ void *g_scratch_addr[MAX_DEVICES];
 size_t a256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct Carve {
-    size_t mask, codes, cnt, pre, bsum, face, tinfo, parent, key, psize, xcol, status, ncl, total;
+    size_t mask, codes, cnt, pre, bsum, face, tinfo, parent, key, psize, xcol, ovf, status, ncl, total;
 };
 
 Carve carve(const hk::TileInfo &ti, const hk::Plan &P) {
@@ -52,7 +52,8 @@ Carve carve(const hk::TileInfo &ti, const hk::Plan &P) {
     c.key = take((size_t)P.piece_cap * 4);
     c.psize = take((size_t)P.piece_cap * 4);
     c.xcol = take((size_t)P.ntiles * (ti.rows / 32) * 2 * 4);
-    c.status = take(4);
+    c.ovf = take((size_t)P.ntiles * 4);
+    c.status = take(8);   // status word, then the count of ovf
     c.ncl = take(8);
     c.total = off;
     return c;
@@ -104,6 +105,8 @@ extern "C" int hk_label_noalloc(const float *phi, int nx, int ny, int nz, const 
     W.psize = reinterpret_cast<int32_t *>(base + c.psize);
     W.xcol = reinterpret_cast<uint32_t *>(base + c.xcol);
     W.status = reinterpret_cast<int32_t *>(base + c.status);
+    W.ovf = reinterpret_cast<int32_t *>(base + c.ovf);
+    W.novf = W.status + 1;
     W.piece_cap = P.piece_cap;
 
     // The array keeps the previous call's contents.  Everything the passes read is

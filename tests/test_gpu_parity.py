@@ -101,6 +101,28 @@ def test_max_clusters_checkerboard(labeller):
             assert_parity(labeller, phi, per, f"checkerboard {shape} {per}")
 
 
+def test_mixed_run_density_tiles(labeller):
+    """Tiles of very different run counts in one lattice: sparse random tiles next to
+    checkerboard tiles (16 runs a row) and tiles whose rows alternate between 16 runs
+    and one full run (few runs, but 16 union pairs a row along y and z), so that the
+    dense tiles are labelled by the second tile pass and joined to the others."""
+    rng = np.random.default_rng(11)
+    nx, ny, nz = 133, 67, 71
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    kind = rng.integers(0, 4, size=((nz + 15) // 16, (ny + 15) // 16, (nx + 31) // 32))
+    k = kind[z // 16, y // 16, x // 32]
+    occ = rng.random((nz, ny, nx)) < 0.3                      # kind 0: p = 0.3
+    occ = np.where(k == 1, (x + y + z) % 2 == 0, occ)         # kind 1: checkerboard
+    occ = np.where(k == 2, (y % 2 == 1) | (x % 2 == 0), occ)  # kind 2: 16-run rows under full rows
+    occ = np.where(k == 3, rng.random((nz, ny, nx)) < 0.6, occ)
+    phi = np.where(occ, 1.0, -1.0).astype(np.float32)
+    for tile in TILES:
+        labeller.set_tile(*tile)
+        for per in [(0, 0, 0), (1, 1, 1), (1, 0, 1)]:
+            assert_parity(labeller, phi, per, f"mixed density tile {tile} {per}")
+    labeller.set_tile(16, 16)
+
+
 def test_block_pattern_and_rods(labeller):
     nx, ny, nz = 64, 48, 40
     z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
