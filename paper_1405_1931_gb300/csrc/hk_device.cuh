@@ -18,7 +18,6 @@
 namespace hk {
 
 constexpr int TX = 32;
-constexpr uint16_t FACE_NONE = 0xFFFF;
 // Run codes (one uint16 per x-run, written by the tile pass, decoded by flatten):
 //   CODE_BOUNDARY | k               a run of boundary piece k of the tile
 //   CODE_BOUNDARY | CODE_ROOT | k   the first run of boundary piece k
@@ -54,7 +53,7 @@ struct Work {
     uint32_t *cnt;      // [nseg] cluster roots per segment (row-major segment order)
     uint32_t *pre;      // [nseg + 1] exclusive prefix of cnt
     uint32_t *bsum;     // [nblocks] scan block sums
-    uint16_t *face;     // [ntiles * face_stride] boundary-piece numbers of face sites
+    uint16_t *face;     // [ntiles * face_stride] per-face lists of boundary-piece numbers
     int4 *tinfo;        // [ntiles] (piece base, piece count, run count, 0) of each tile
     int32_t *parent;    // [piece_cap] union-find parent over boundary pieces; tile t owns
                         // the slice [t * MAX_BOUNDARY, t * MAX_BOUNDARY + piece count)
@@ -96,14 +95,21 @@ struct TileShape {
     // second pass sized for MAXRUNS.
     static constexpr int MR_FAST = 10 * R;
     static constexpr int NT = R;                 // threads per CTA: one per row
-    // face layout inside a tile's face block
-    static constexpr int OFF_LX = 0;
-    static constexpr int OFF_HX = R;
-    static constexpr int OFF_LY = 2 * R;                 // [lz][x]
-    static constexpr int OFF_HY = 2 * R + TX * TZ;
-    static constexpr int OFF_LZ = 2 * R + 2 * TX * TZ;   // [ly][x]
-    static constexpr int OFF_HZ = 2 * R + 2 * TX * TZ + TX * TY;
-    static constexpr int FACE_STRIDE = 2 * R + 2 * TX * TZ + 2 * TX * TY;
+    // Face lists inside a tile's face block: 8 counts (one per face, two unused),
+    // then per face the boundary numbers of its emitted connected sites.  Emitted
+    // sites are pairwise non-adjacent along x (y and z faces: at most 16 a row) or
+    // along y (x faces: at most R / 2).
+    static constexpr int OFF_CNT = 0;                     // [6] lo-x, hi-x, lo-y, hi-y, lo-z, hi-z
+    static constexpr int OFF_LX = 8;
+    static constexpr int OFF_HX = 8 + R / 2;
+    static constexpr int OFF_LY = 8 + R;
+    static constexpr int OFF_HY = 8 + R + 16 * TZ;
+    static constexpr int OFF_LZ = 8 + R + 32 * TZ;
+    static constexpr int OFF_HZ = 8 + R + 32 * TZ + 16 * TY;
+    static constexpr int FACE_STRIDE = 8 + R + 32 * TZ + 32 * TY;
+    // rows with ly = 0 inside a 32-row word (x-face lists)
+    static constexpr uint32_t LY0 = TY == 8 ? 0x01010101u : TY == 16 ? 0x00010001u : 0x00000001u;
+    static_assert(TY == 8 || TY == 16 || TY == 32, "tile rows along y");
     // Upper bound on boundary pieces of one tile: pieces touching one face are
     // pairwise non-adjacent on that face's 2D grid, so at most ceil(area/2) of
     // them touch it.

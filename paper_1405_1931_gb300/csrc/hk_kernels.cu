@@ -158,6 +158,7 @@ struct LabelSmem {
     uint32_t nylo[TZ], nyhi[TZ];           // neighbour rows across the y faces, per plane
     uint32_t nzlo[TY], nzhi[TY];           // neighbour rows across the z faces, per row
     uint32_t nxlo[SH::R / 32], nxhi[SH::R / 32];   // neighbour columns across the x faces
+    uint32_t xo0[SH::R / 32], xol[SH::R / 32];     // this tile's first and last column
     static_assert(TZ <= 16 && TY <= 32 && SH::R / 32 <= 16 && SH::NT >= 64, "face loads use threads 0..63");
     uint32_t chunkbal[CAP / 32];           // boundary-root ballot of each chunk of 32 run ids
     uint32_t chunkint[CAP / 32];           // interior-root ballot of each chunk
@@ -210,6 +211,14 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
         const uint32_t m = W.mask[t * R + r];
         S.m[r] = m;
         const uint32_t rs = run_starts(m);
+        {
+            const uint32_t c0 = __ballot_sync(0xffffffffu, m & 1u);
+            const uint32_t cl = __ballot_sync(0xffffffffu, (m >> g.lastX) & 1u);
+            if ((tid & 31) == 0) {
+                S.xo0[tid >> 5] = c0;
+                S.xol[tid >> 5] = cl;
+            }
+        }
 
         // Occupancy across the six faces, from the neighbour tiles' masks (the
         // occupancy pass has written all of them).  A face site is connected when
@@ -431,87 +440,99 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
             C[i] = c;
         }
 
-        // face summaries: boundary number of the piece holding each connected face site
-        uint16_t *F = W.face + t * SH::FACE_STRIDE;
-        auto site_k = [&](int row, uint32_t conn_bits, int x) -> uint16_t {
-            if (!((conn_bits >> x) & 1u)) return FACE_NONE;
-            const uint32_t mm = S.m[row];
-            return (uint16_t)piece_k(S.par, run_of(S.rbase[row], run_starts(mm), x));
-        };
-        if (g.extXlo) F[SH::OFF_LX + r] = site_k(r, ((S.nxlo[r >> 5] >> (r & 31)) & 1u) ? m : 0u, 0);
-        if (g.extXhi) F[SH::OFF_HX + r] = site_k(r, ((S.nxhi[r >> 5] >> (r & 31)) & 1u) ? m : 0u, g.lastX);
-        for (int e = r; e < TX * TZ; e += NT) {
-            const int fz = e / TX, x = e % TX;
-            if (g.extYlo) F[SH::OFF_LY + e] = site_k(fz * TY, S.m[fz * TY] & S.nylo[fz], x);
-            if (g.extYhi) F[SH::OFF_HY + e] = site_k(fz * TY + g.lastY, S.m[fz * TY + g.lastY] & S.nyhi[fz], x);
-        }
-        for (int e = r; e < TX * TY; e += NT) {
-            const int fy = e / TX, x = e % TX;
-            if (g.extZlo) F[SH::OFF_LZ + e] = site_k(fy, S.m[fy] & S.nzlo[fy], x);
-            if (g.extZhi) F[SH::OFF_HZ + e] = site_k(g.lastZ * TY + fy, S.m[g.lastZ * TY + fy] & S.nzhi[fy], x);
+        // Face lists.  A face site is connected when it and its neighbour across the
+        // face are occupied.  Adjacent connected sites of a face lie in one piece on
+        // either side, so one union per component of connected face sites suffices: a
+        // connected site is emitted unless its face neighbour at lower x (y and z
+        // faces) or at lower y or z (x faces) is connected too, which keeps the
+        // lowest site of every component.  Both tiles of a face compute the same
+        // connected sites, so their lists pair up entry by entry.  Warps take the faces
+        // in turn (lo-x, hi-x, lo-y, hi-y, lo-z, hi-z); lane j owns one 32-bit word.
+        {
+            const int lane = tid & 31;
+            for (int f = tid >> 5; f < 6; f += NT / 32) {
+                const int hi = f & 1, axis = f >> 1;
+                const bool ext = axis == 0 ? (hi ? g.extXhi : g.extXlo)
+                               : axis == 1 ? (hi ? g.extYhi : g.extYlo) : (hi ? g.extZhi : g.extZlo);
+                uint32_t c = 0;
+                int row0 = 0;   // y and z faces: the row of this lane's word
+                if (ext) {
+                    if (axis == 0) {
+                        if (lane < R / 32) c = hi ? (S.xol[lane] & S.nxhi[lane]) : (S.xo0[lane] & S.nxlo[lane]);
+                    } else if (axis == 1) {
+                        row0 = lane * TY + (hi ? g.lastY : 0);
+                        if (lane < TZ) c = S.m[row0] & (hi ? S.nyhi[lane] : S.nylo[lane]);
+                    } else {
+                        row0 = (hi ? g.lastZ : 0) * TY + lane;
+                        if (lane < TY) c = S.m[row0] & (hi ? S.nzhi[lane] : S.nzlo[lane]);
+                    }
+                }
+                uint32_t prev = __shfl_up_sync(0xffffffffu, c, 1);
+                if (lane == 0) prev = 0;
+                uint32_t e;
+                if (axis == 0) {
+                    // bit i of word j is row 32 j + i; rows r - 1 (same plane) and r - TY
+                    const uint32_t ym = ((c << 1) | (prev >> 31)) & ~SH::LY0;
+                    const uint32_t zm = TY == 32 ? prev : ((c << (TY & 31)) | (prev >> ((32 - TY) & 31)));
+                    e = c & ~ym & ~zm;
+                } else {
+                    e = c & ~(c << 1) & ~prev;
+                }
+                const int cnt = __popc(e);
+                int inc = cnt;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int u = __shfl_up_sync(0xffffffffu, inc, d);
+                    if (lane >= d) inc += u;
+                }
+                const int n = __shfl_sync(0xffffffffu, inc, 31);
+                uint16_t *F = W.face + t * SH::FACE_STRIDE;
+                const int off = f == 0 ? SH::OFF_LX : f == 1 ? SH::OFF_HX : f == 2 ? SH::OFF_LY
+                              : f == 3 ? SH::OFF_HY : f == 4 ? SH::OFF_LZ : SH::OFF_HZ;
+                int j = off + inc - cnt;
+                while (e) {
+                    const int b = __ffs(e) - 1;
+                    e &= e - 1;
+                    const int row = axis == 0 ? lane * 32 + b : row0;
+                    const int x = axis == 0 ? (hi ? g.lastX : 0) : b;
+                    F[j++] = (uint16_t)piece_k(S.par, run_of(S.rbase[row], run_starts(S.m[row]), x));
+                }
+                if (lane == 0) F[SH::OFF_CNT + f] = (uint16_t)n;
+            }
         }
         __syncthreads();
     }
 }
 
 // --------------------------------------------------------------------------------------
-// K2: face merge.  Each tile joins its low face along axis blockIdx.y with the high
-// face of its lower neighbour (for tile 0 of a periodic axis: with the last tile,
-// the wrap).  One face per CTA and all face entries loaded before any union, so the
-// union chains of many faces are in flight together.
+// K2: face merge.  One warp per (tile, axis): the tile's low face list along the
+// axis is joined entry by entry with the high face list of its lower neighbour (for
+// tile 0 of a periodic axis: the last tile, the wrap).
 // --------------------------------------------------------------------------------------
 template <int TY, int TZ, int NL>
-__global__ void __launch_bounds__(TY * TZ)
-k_face_merge(const __grid_constant__ LatBatch<NL> B, Work W) {
+__global__ void __launch_bounds__(256)
+k_face_merge(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
     using SH = TileShape<TY, TZ>;
-    constexpr int NT = SH::NT;
-    constexpr int PY = (TX * TZ + NT - 1) / NT, PZ = (TX * TY + NT - 1) / NT;   // entries per thread
-    const int64_t t = blockIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t item = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (item >= 3 * ntiles) return;
+    const int64_t t = item / 3;
+    const int axis = (int)(item - 3 * t);
     const LatDev &L = B.lat[(NL == 1) ? 0 : find_lattice(B.lat, B.n, t)];
     const TileGeo g = tile_geo<TY, TZ>(L, t);
-    const int base = W.tinfo[t].x;
-    const uint16_t *F = W.face + t * SH::FACE_STRIDE;
-    const int tid = threadIdx.x, lane = tid & 31;
+    if (!(axis == 0 ? g.extXlo : axis == 1 ? g.extYlo : g.extZlo)) return;
     const int64_t plane = (int64_t)L.nbx * L.nby;
-    const int64_t tx = g.bx > 0 ? t - 1 : t + (L.nbx - 1);
-    const int64_t ty = g.by > 0 ? t - L.nbx : t + (int64_t)(L.nby - 1) * L.nbx;
-    const int64_t tz = g.bz > 0 ? t - plane : t + (int64_t)(L.nbz - 1) * plane;
-    // load every face entry this thread joins before the first union
-    uint32_t px = 0xffffffffu, py[PY], pz[PZ];
-    int bx_ = 0, by_ = 0, bz_ = 0;
-    if (g.extXlo) {
-        bx_ = W.tinfo[tx].x;
-        px = ((uint32_t)F[SH::OFF_LX + tid] << 16) | W.face[tx * SH::FACE_STRIDE + SH::OFF_HX + tid];
-    }
-#pragma unroll
-    for (int j = 0; j < PY; ++j) {
-        const int e = tid + j * NT;
-        py[j] = 0xffffffffu;
-        if (g.extYlo && e < TX * TZ)
-            py[j] = ((uint32_t)F[SH::OFF_LY + e] << 16) | W.face[ty * SH::FACE_STRIDE + SH::OFF_HY + e];
-    }
-#pragma unroll
-    for (int j = 0; j < PZ; ++j) {
-        const int e = tid + j * NT;
-        pz[j] = 0xffffffffu;
-        if (g.extZlo && e < TX * TY)
-            pz[j] = ((uint32_t)F[SH::OFF_LZ + e] << 16) | W.face[tz * SH::FACE_STRIDE + SH::OFF_HZ + e];
-    }
-    if (g.extYlo) by_ = W.tinfo[ty].x;
-    if (g.extZlo) bz_ = W.tinfo[tz].x;
-    auto join = [&](uint32_t pr, int bp, bool dedup) {
-        // y/z faces list consecutive x in each row (a warp covers one row): a run of
-        // equal pairs along x is joined once
-        const uint32_t prev = __shfl_up_sync(0xffffffffu, pr, 1);
-        const uint16_t a = (uint16_t)(pr >> 16), b = (uint16_t)pr;
-        if (a != FACE_NONE && b != FACE_NONE && !(dedup && lane != 0 && prev == pr))
-            g_union(W.parent, W.key, base + a, bp + b, W.piece_cap, W.status);
-    };
-    join(px, bx_, false);
-#pragma unroll
-    for (int j = 0; j < PY; ++j) join(py[j], by_, true);
-#pragma unroll
-    for (int j = 0; j < PZ; ++j) join(pz[j], bz_, true);
+    const int64_t nb = axis == 0 ? (g.bx > 0 ? t - 1 : t + (L.nbx - 1))
+                     : axis == 1 ? (g.by > 0 ? t - L.nbx : t + (int64_t)(L.nby - 1) * L.nbx)
+                                 : (g.bz > 0 ? t - plane : t + (int64_t)(L.nbz - 1) * plane);
+    const uint16_t *F = W.face + t * SH::FACE_STRIDE;
+    const uint16_t *G = W.face + nb * SH::FACE_STRIDE;
+    const int n = F[SH::OFF_CNT + 2 * axis];
+    const int lo = axis == 0 ? SH::OFF_LX : axis == 1 ? SH::OFF_LY : SH::OFF_LZ;
+    const int hi = axis == 0 ? SH::OFF_HX : axis == 1 ? SH::OFF_HY : SH::OFF_HZ;
+    const int base = W.tinfo[t].x, bbase = W.tinfo[nb].x;
+    for (int i = lane; i < n; i += 32)
+        g_union(W.parent, W.key, base + F[lo + i], bbase + G[hi + i], W.piece_cap, W.status);
 }
 
 // --------------------------------------------------------------------------------------
@@ -876,7 +897,7 @@ static cudaError_t launch_all(const LatDev *lats, int n, const Plan &P, const Wo
     k_tile_label<TY, TZ, NL, false><<<(unsigned)(P.ntiles < grid1b ? P.ntiles : grid1b), SH::NT, smem1b, st>>>(
         B, W, P.ntiles);
     mark(2);
-    k_face_merge<TY, TZ, NL><<<(unsigned)P.ntiles, SH::NT, 0, st>>>(B, W);
+    k_face_merge<TY, TZ, NL><<<(unsigned)((3 * P.ntiles + 7) / 8), 256, 0, st>>>(B, W, P.ntiles);
     mark(3);
     k_piece_finalize<NL><<<(unsigned)P.ntiles, 256, 0, st>>>(B, W);
     mark(4);
