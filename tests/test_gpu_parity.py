@@ -123,6 +123,21 @@ def test_mixed_run_density_tiles(labeller):
     labeller.set_tile(16, 16)
 
 
+def test_many_boundary_pieces(labeller):
+    """Short rods along z on the (x + y) even columns, three sites at each end of
+    every 8-plane slab: with 32x32x8 tiles each tile holds 1024 boundary pieces
+    (two per column, each joined to the next slab across the z face)."""
+    nx, ny, nz = 64, 64, 24
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    occ = ((x + y) % 2 == 0) & np.isin(z % 8, [0, 1, 2, 5, 6, 7])
+    phi = np.where(occ, 1.0, -1.0).astype(np.float32)
+    for tile in TILES:
+        labeller.set_tile(*tile)
+        for per in [(0, 0, 0), (1, 1, 1)]:
+            assert_parity(labeller, phi, per, f"boundary pieces tile {tile} {per}")
+    labeller.set_tile(16, 16)
+
+
 def test_block_pattern_and_rods(labeller):
     nx, ny, nz = 64, 48, 40
     z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
