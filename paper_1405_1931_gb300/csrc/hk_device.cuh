@@ -226,23 +226,25 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 // Every store to par[] lowers it to an ancestor (a root is linked to a smaller id
 // of the other tree, halving stores a grandparent, compression stores the root),
 // so par[i] <= i always holds and a find walks strictly decreasing ids: it ends
-// within i steps by construction.  The union's retry loop is the one that depends
-// on other threads, and it keeps an explicit bound.
+// within i steps by construction.  For the same reason the finds use plain loads: a
+// value that another thread has since lowered is still an ancestor.  Linking goes
+// through atomicMin, whose old value tells whether a root was still a root.  The
+// union's retry loop is the one that depends on other threads, and it keeps an
+// explicit bound.
 
 // read-only find: used by compression, where finds run while others store final
 // roots (a halving store there could overwrite a final root with an ancestor)
-__device__ __forceinline__ int s_find_ro(const int *par, int x, int, int32_t *) {
-    const volatile int *vp = par;
-    int p = vp[x];
+__device__ __forceinline__ int s_find_ro(const int *par, int x) {
+    int p = par[x];
     while (p != x) {
         x = p;
-        p = vp[x];
+        p = par[x];
     }
     return x;
 }
 
 // find with path halving (during the unions)
-__device__ __forceinline__ int s_find(volatile int *par, int x) {
+__device__ __forceinline__ int s_find(int *par, int x) {
     int p = par[x];
     while (p != x) {
         const int gp = par[p];
@@ -256,10 +258,9 @@ __device__ __forceinline__ int s_find(volatile int *par, int x) {
 
 // Each retry strictly lowers max(a, b), so at most `cap` rounds.
 __device__ __forceinline__ void s_union(int *par, int a, int b, int cap, int32_t *status) {
-    volatile int *vp = par;
     for (int it = 0; it <= cap; ++it) {
-        a = s_find(vp, a);
-        b = s_find(vp, b);
+        a = s_find(par, a);
+        b = s_find(par, b);
         if (a == b) return;
         const int hi = a > b ? a : b, lo = a > b ? b : a;
         const int old = atomicMin(&par[hi], lo);

@@ -321,7 +321,7 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
         // run).  The finds are read-only, so storing final roots while others still
         // search is safe.
         for (int i = tid; i < total; i += NT) {
-            S.par[i] = s_find_ro(S.par, i, total, W.status);
+            S.par[i] = s_find_ro(S.par, i);
             S.aux[i] = 0;
         }
         __syncthreads();
