@@ -137,11 +137,12 @@ __device__ __forceinline__ int find_lattice(const LatDev *lats, int nlat, int64_
 template <int TY, int TZ>
 __device__ __forceinline__ TileGeo tile_geo(const LatDev &L, int64_t t) {
     TileGeo g;
-    int64_t lt = t - L.tile0;
-    g.bx = (int)(lt % L.nbx);
-    int64_t q = lt / L.nbx;
-    g.by = (int)(q % L.nby);
-    g.bz = (int)(q / L.nby);
+    // a lattice has fewer than 2^31 sites, so its tile index fits in 32 bits
+    const uint32_t lt = (uint32_t)(t - L.tile0);
+    const uint32_t q = lt / (uint32_t)L.nbx;
+    g.bx = (int)(lt - q * (uint32_t)L.nbx);
+    g.bz = (int)(q / (uint32_t)L.nby);
+    g.by = (int)(q - (uint32_t)g.bz * (uint32_t)L.nby);
     g.x0 = g.bx * TX; g.y0 = g.by * TY; g.z0 = g.bz * TZ;
     g.lastX = min(TX, L.nx - g.x0) - 1;
     g.lastY = min(TY, L.ny - g.y0) - 1;

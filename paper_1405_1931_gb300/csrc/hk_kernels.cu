@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(256) k_occupancy_tma(const __grid_constant__ T
                 if (lane == j) mine = w;
             }
             W.mask[t * R + r0 + lane] = mine;
-            const int lastX = min(TX, L.nx - (int)(t % L.nbx) * TX) - 1;
+            const int lastX = min(TX, L.nx - (int)((uint32_t)t % (uint32_t)L.nbx) * TX) - 1;
             const uint32_t c0 = __ballot_sync(0xffffffffu, mine & 1u);
             const uint32_t cl = __ballot_sync(0xffffffffu, (mine >> lastX) & 1u);
             if (lane == 0) {
@@ -695,9 +695,10 @@ template <int TY, int TZ>
 struct FlatSmem {
     using SH = TileShape<TY, TZ>;
     alignas(128) int32_t stage[SH::SITES];    // labels [lz][ly][x] (TMA store source)
+    static constexpr int GL = SH::MAX_BOUNDARY < 512 ? SH::MAX_BOUNDARY : 512;   // staged boundary pieces
     uint16_t code[SH::MAXRUNS];
-    int gl[SH::MAX_BOUNDARY];                 // label of each boundary piece's cluster
-    int gsize[SH::MAX_BOUNDARY];              // cluster size if the piece is the cluster root, else -1
+    int gl[GL];                               // label of each boundary piece's cluster
+    int gsize[GL];                            // cluster size if the piece is the cluster root, else -1
     int warp_tmp[32];
     int hist[32];
 };
@@ -709,7 +710,7 @@ __device__ __forceinline__ int site_of(const TileGeo &g, const LatDev &L, int po
 }
 
 template <int TY, int TZ, int NL>
-__global__ void __launch_bounds__(TY * TZ)
+__global__ void __launch_bounds__(TY * TZ, 1280 / (TY * TZ))
 k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapPair tm, Work W, int64_t ntiles) {
     using SH = TileShape<TY, TZ>;
     constexpr int R = SH::R, NT = SH::NT, NW = NT / 32, MR = SH::MAXRUNS;
@@ -751,7 +752,7 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapPa
 
         const uint16_t *C = W.codes + t * MR;
         for (int i = tid; i < total; i += NT) S.code[i] = C[i];
-        for (int k = tid; k < nb; k += NT) {
+        for (int k = tid; k < nb && k < FlatSmem<TY, TZ>::GL; k += NT) {
             S.gl[k] = __ldg(W.key + base + k);       // cluster label (written by piece_finalize)
             S.gsize[k] = __ldg(W.psize + base + k);  // cluster size at the root piece, else -1
         }
@@ -774,8 +775,13 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapPa
             int lab, size = -1;
             if (c & CODE_BOUNDARY) {
                 const int k = c & CODE_LOW;
-                lab = S.gl[k];
-                if (c & CODE_ROOT) size = S.gsize[k];
+                if (k < FlatSmem<TY, TZ>::GL) {
+                    lab = S.gl[k];
+                    if (c & CODE_ROOT) size = S.gsize[k];
+                } else {
+                    lab = __ldg(W.key + base + k);
+                    if (c & CODE_ROOT) size = __ldg(W.psize + base + k);
+                }
             } else if (c & CODE_ROOT) {
                 lab = site_row + x0;
                 size = c & CODE_LOW;
