@@ -60,11 +60,11 @@ Layout make_layout(const TileInfo &ti, const Plan &P) {
     Layout L{};
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
-    const int64_t nb = (P.nseg + 4096) / 4096;
+    const int64_t nb = (P.nrows + 4096) / 4096;
     L.mask = take((size_t)P.ntiles * ti.rows * 4);
     L.codes = take((size_t)P.ntiles * ti.maxruns * 2);
-    L.cnt = take((size_t)P.nseg * 4);
-    L.pre = take((size_t)(P.nseg + 1) * 4);
+    L.cnt = take((size_t)P.nseg);
+    L.pre = take((size_t)(P.nrows + 1) * 4);
     L.bsum = take((size_t)nb * 4);
     L.face = take((size_t)P.ntiles * ti.face_stride * 2);
     L.tinfo = take((size_t)P.ntiles * 16);
@@ -84,6 +84,7 @@ void add_lattice(const TileInfo &ti, int nx, int ny, int nz, Plan &P) {
     const int64_t nbx = ceil_div(nx, hk::TX), nby = ceil_div(ny, ti.ty), nbz = ceil_div(nz, ti.tz);
     P.ntiles += nbx * nby * nbz;
     P.nseg += nbx * (int64_t)ny * nz;
+    P.nrows += (int64_t)ny * nz;
 }
 
 int fail_cuda(hk_ctx *ctx, cudaError_t e) {
@@ -166,8 +167,9 @@ void make_tmaps(const hk_lattice &l, int ty, int tz, hk::TmapPair &tm) {
            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return;
+    // labels leave a staged tile laid out with the 128-byte swizzle (box rows are 128 bytes)
     if (fn(&tm.labels, CU_TENSOR_MAP_DATA_TYPE_INT32, 3, l.labels, dims, strides, box, estr,
-           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return;
     tm.valid = 1;
@@ -211,7 +213,7 @@ int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st) {
         int c0 = 0;
         while (c0 < n) {
             chunk_start.push_back(c0);
-            Plan P{0, 0, 0};
+            Plan P{0, 0, 0, 0};
             int c1 = c0;
             while (c1 < n && c1 - c0 < hk::MAX_LAT_PER_LAUNCH) {
                 Plan Q = P;
@@ -227,7 +229,7 @@ int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st) {
     // size the workspace for the largest chunk
     size_t need = 0;
     for (size_t c = 0; c + 1 < chunk_start.size(); ++c) {
-        Plan P{0, 0, 0};
+        Plan P{0, 0, 0, 0};
         for (int i = chunk_start[c]; i < chunk_start[c + 1]; ++i) add_lattice(ti, lats[i].nx, lats[i].ny, lats[i].nz, P);
         P.piece_cap = P.ntiles * ti.max_boundary;
         need = std::max(need, make_layout(ti, P).total);
@@ -246,7 +248,7 @@ int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st) {
     for (size_t c = 0; c + 1 < chunk_start.size(); ++c) {
         const int c0 = chunk_start[c];
         const int cn = chunk_start[c + 1] - c0;
-        Plan P{0, 0, 0};
+        Plan P{0, 0, 0, 0};
         std::vector<LatDev> dev(cn);
         for (int i = 0; i < cn; ++i) {
             const hk_lattice &l = lats[c0 + i];
@@ -265,6 +267,7 @@ int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st) {
             d.nbz = (int)ceil_div(l.nz, ti.tz);
             d.tile0 = P.ntiles;
             d.seg0 = P.nseg;
+            d.row0 = P.nrows;
             add_lattice(ti, l.nx, l.ny, l.nz, P);
         }
         P.piece_cap = P.ntiles * ti.max_boundary;
@@ -273,7 +276,7 @@ int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st) {
         Work W;
         W.mask = reinterpret_cast<uint32_t *>(base + Ly.mask);
         W.codes = reinterpret_cast<uint16_t *>(base + Ly.codes);
-        W.cnt = reinterpret_cast<uint32_t *>(base + Ly.cnt);
+        W.cnt = reinterpret_cast<uint8_t *>(base + Ly.cnt);
         W.pre = reinterpret_cast<uint32_t *>(base + Ly.pre);
         W.bsum = reinterpret_cast<uint32_t *>(base + Ly.bsum);
         W.face = reinterpret_cast<uint16_t *>(base + Ly.face);
@@ -360,7 +363,7 @@ size_t hk_workspace_bytes(int nx, int ny, int nz) {
     if (nx < 1 || ny < 1 || nz < 1 || (int64_t)nx * ny * nz >= MAX_SITES) return 0;
     TileInfo ti;
     hk::tile_info(DEFAULT_TY, DEFAULT_TZ, ti);
-    Plan P{0, 0, 0};
+    Plan P{0, 0, 0, 0};
     add_lattice(ti, nx, ny, nz, P);
     P.piece_cap = P.ntiles * ti.max_boundary;
     return make_layout(ti, P).total;

@@ -29,8 +29,9 @@ constexpr uint16_t CODE_ROOT = 0x4000;
 constexpr uint16_t CODE_LOW = 0x3fff;
 
 // One lattice of a launch.  Every pass works on the concatenated tiles of all
-// lattices; tile0/seg0 locate this lattice's slice of the global tile and
-// segment index spaces.  A segment is one tile row: 32 consecutive x sites.
+// lattices; tile0/seg0/row0 locate this lattice's slice of the global tile,
+// segment and row index spaces.  A segment is one tile row: 32 consecutive x
+// sites; a row is one lattice row (all x at one y, z).
 struct LatDev {
     const float *phi;
     int32_t *labels;
@@ -44,14 +45,15 @@ struct LatDev {
     int pad_;
     int64_t tile0;   // first global tile id
     int64_t seg0;    // first global segment id (row-major: ((z*ny + y)*nbx + bx))
+    int64_t row0;    // first global row id (z*ny + y)
 };
 
 // Workspace pointers shared by all passes of one launch.
 struct Work {
     uint32_t *mask;     // [ntiles * R] occupancy words, tile-major (tile t, row r)
     uint16_t *codes;    // [ntiles * MAXRUNS] one code per run (CODE_* above)
-    uint32_t *cnt;      // [nseg] cluster roots per segment (row-major segment order)
-    uint32_t *pre;      // [nseg + 1] exclusive prefix of cnt
+    uint8_t *cnt;       // [nseg] cluster roots per segment (row-major segment order; <= 16)
+    uint32_t *pre;      // [nrows + 1] exclusive prefix of the roots per lattice row
     uint32_t *bsum;     // [nblocks] scan block sums
     uint16_t *face;     // [ntiles * face_stride] per-face lists of boundary-piece numbers
     int4 *tinfo;        // [ntiles] (piece base, piece count, run count, 0) of each tile
@@ -130,6 +132,16 @@ __device__ __forceinline__ int find_lattice(const LatDev *lats, int nlat, int64_
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
         if (lats[mid].tile0 <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// the lattice holding global row q
+__device__ __forceinline__ int find_lattice_row(const LatDev *lats, int nlat, int64_t q) {
+    int lo = 0, hi = nlat - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (lats[mid].row0 <= q) lo = mid; else hi = mid - 1;
     }
     return lo;
 }
@@ -284,6 +296,22 @@ __device__ __forceinline__ void join_rows(int *par, uint32_t m, int rb, uint32_t
         os &= os - 1;
         s_union(par, run_of(rb, rs, x), run_of(rbq, rsq, x), cap, status);
     }
+}
+
+// Sum of the n bytes at base[start, start + n), read as the aligned 32-bit words that
+// cover them (the bytes outside the range are masked off).  The array must extend to
+// the end of the word holding its last byte.
+__device__ __forceinline__ uint32_t bytes_sum(const uint8_t *base, int64_t start, int64_t n) {
+    uint32_t s = 0;
+    const int64_t e = start + n;
+    for (int64_t w = start & ~(int64_t)3; w < e; w += 4) {
+        const uint32_t v = *reinterpret_cast<const uint32_t *>(base + w);
+        const int lo = start > w ? (int)(start - w) : 0;    // keep bytes [lo, hi) of the word
+        const int hi = e - w < 4 ? (int)(e - w) : 4;
+        const uint32_t keep = (hi == 4 ? 0xffffffffu : ((1u << (8 * hi)) - 1u)) & ~((1u << (8 * lo)) - 1u);
+        s = __dp4a(v & keep, 0x01010101u, s);
+    }
+    return s;
 }
 
 // Block-wide exclusive scan of one int per thread (blockDim.x == NT, NT % 32 == 0, NT <= 992).

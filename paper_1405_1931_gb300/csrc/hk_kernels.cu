@@ -421,7 +421,7 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
                 }
             }
             const int64_t seg = L.seg0 + ((int64_t)(g.z0 + lz) * L.ny + (g.y0 + ly)) * L.nbx + g.bx;
-            W.cnt[seg] = (uint32_t)interior;
+            W.cnt[seg] = (uint8_t)interior;
         }
 
         // one code per run (CODE_* encoding)
@@ -536,19 +536,20 @@ k_face_merge(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
 }
 
 // --------------------------------------------------------------------------------------
-// K3: piece finalize (one CTA per tile, one piece per thread).  Size additions into
+// K3: piece finalize (one warp per tile, one piece per lane).  Size additions into
 // the same cluster root are combined per warp first, because the percolating
 // cluster collects pieces from most tiles.
 // --------------------------------------------------------------------------------------
 template <int NL>
 __global__ void __launch_bounds__(256)
-k_piece_finalize(const __grid_constant__ LatBatch<NL> B, Work W) {
-    const int64_t t = blockIdx.x;
+k_piece_finalize(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
+    const int64_t t = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
+    if (t >= ntiles) return;
     const int4 ti = W.tinfo[t];
     if (ti.y == 0) return;
     const LatDev &L = B.lat[(NL == 1) ? 0 : find_lattice(B.lat, B.n, t)];
-    for (int j0 = (threadIdx.x & ~31); j0 < ti.y; j0 += 256) {
+    for (int j0 = 0; j0 < ti.y; j0 += 32) {
         const int j = j0 + lane;
         const bool valid = j < ti.y;
         const int pid = ti.x + j;
@@ -568,7 +569,8 @@ k_piece_finalize(const __grid_constant__ LatBatch<NL> B, Work W) {
                 const int q = k / L.nx, x = k - q * L.nx;
                 const int y = q % L.ny, z = q / L.ny;
                 const int64_t seg = L.seg0 + ((int64_t)z * L.ny + y) * L.nbx + (x >> 5);
-                atomicAdd(W.cnt + seg, 1u);
+                // one byte per segment (at most 16 roots): add to it inside its aligned word
+                atomicAdd(reinterpret_cast<unsigned int *>(W.cnt + (seg & ~(int64_t)3)), 1u << (8 * (int)(seg & 3)));
             }
         }
         const int target = (valid && root != pid) ? root : -1;
@@ -579,19 +581,29 @@ k_piece_finalize(const __grid_constant__ LatBatch<NL> B, Work W) {
 }
 
 // --------------------------------------------------------------------------------------
-// S1-S3: exclusive scan of the per-segment root counts
+// S1-S3: exclusive scan of the cluster roots per lattice row (the sum of the row's
+// segment counts); ranks inside a row are completed by flatten from the segment
+// counts before its own.
 // --------------------------------------------------------------------------------------
 constexpr int SCAN_NT = 256;
 constexpr int SCAN_PER = 16;
 constexpr int SCAN_CH = SCAN_NT * SCAN_PER;
 
-__global__ void __launch_bounds__(SCAN_NT) k_scan_reduce(const uint32_t *cnt, int64_t n, uint32_t *bsum) {
+template <int NL>
+__device__ __forceinline__ uint32_t row_roots(const LatBatch<NL> &B, const uint8_t *cnt, int64_t q) {
+    const LatDev &L = B.lat[(NL == 1) ? 0 : find_lattice_row(B.lat, B.n, q)];
+    return bytes_sum(cnt, L.seg0 + (q - L.row0) * L.nbx, L.nbx);
+}
+
+template <int NL>
+__global__ void __launch_bounds__(SCAN_NT) k_scan_reduce(const __grid_constant__ LatBatch<NL> B,
+                                                         const uint8_t *cnt, int64_t n, uint32_t *bsum) {
     __shared__ uint32_t red[SCAN_NT / 32];
     const int64_t b0 = (int64_t)blockIdx.x * SCAN_CH;
     uint32_t s = 0;
     for (int j = 0; j < SCAN_PER; ++j) {
         const int64_t i = b0 + (int64_t)j * SCAN_NT + threadIdx.x;
-        if (i < n) s += cnt[i];
+        if (i < n) s += row_roots(B, cnt, i);
     }
     for (int d = 16; d; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -637,8 +649,9 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t *bsum, int64_t nb
     }
 }
 
-__global__ void __launch_bounds__(SCAN_NT) k_scan_apply(const uint32_t *cnt, int64_t n, const uint32_t *bsum,
-                                                        uint32_t *pre) {
+template <int NL>
+__global__ void __launch_bounds__(SCAN_NT) k_scan_apply(const __grid_constant__ LatBatch<NL> B, const uint8_t *cnt,
+                                                        int64_t n, const uint32_t *bsum, uint32_t *pre) {
     __shared__ uint32_t wsum[SCAN_NT / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t b0 = (int64_t)blockIdx.x * SCAN_CH + (int64_t)threadIdx.x * SCAN_PER;
@@ -647,7 +660,7 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_apply(const uint32_t *cnt, int
 #pragma unroll
     for (int j = 0; j < SCAN_PER; ++j) {
         const int64_t i = b0 + j;
-        v[j] = i < n ? cnt[i] : 0u;
+        v[j] = i < n ? row_roots(B, cnt, i) : 0u;
         s += v[j];
     }
     uint32_t inc = s;
@@ -683,19 +696,24 @@ __global__ void k_lattice_finish(const __grid_constant__ LatBatch<NL> B, Work W)
     const LatDev &L = B.lat[l];
     if (threadIdx.x < 32 && L.hist) L.hist[threadIdx.x] = 0;
     if (threadIdx.x == 0 && L.ncl) {
-        const int64_t nseg = (int64_t)L.nz * L.ny * L.nbx;
-        L.ncl[0] = (int64_t)W.pre[L.seg0 + nseg] - (int64_t)W.pre[L.seg0];
+        // uint32 difference: the prefix may wrap over a launch, a lattice's count does not
+        L.ncl[0] = (int64_t)(uint32_t)(W.pre[L.row0 + (int64_t)L.nz * L.ny] - W.pre[L.row0]);
     }
 }
 
 // --------------------------------------------------------------------------------------
 // K4: flatten (decode run codes; no union-find)
 // --------------------------------------------------------------------------------------
+// The staged tile uses the TMA 128-byte swizzle: in each tile row (128 bytes) the
+// 16-byte chunk index is XORed with the row index mod 8, so that threads writing the
+// same x of consecutive rows hit different banks.
+__device__ __forceinline__ int stage_idx(int row, int x) { return row * 32 + (x ^ ((row & 7) << 2)); }
+
 template <int TY, int TZ>
 struct FlatSmem {
     using SH = TileShape<TY, TZ>;
-    alignas(128) int32_t stage[SH::SITES];    // labels [lz][ly][x] (TMA store source)
-    static constexpr int GL = SH::MAX_BOUNDARY < 512 ? SH::MAX_BOUNDARY : 512;   // staged boundary pieces
+    alignas(1024) int32_t stage[SH::SITES];   // labels [lz][ly][x], swizzled (TMA store source)
+    static constexpr int GL = SH::MAX_BOUNDARY < 384 ? SH::MAX_BOUNDARY : 384;   // staged boundary pieces
     uint16_t code[SH::MAXRUNS];
     int gl[GL];                               // label of each boundary piece's cluster
     int gsize[GL];                            // cluster size if the piece is the cluster root, else -1
@@ -717,7 +735,8 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapPa
     extern __shared__ __align__(128) unsigned char smem_raw[];
     FlatSmem<TY, TZ> &S = *reinterpret_cast<FlatSmem<TY, TZ> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const bool use_tma = (NL == 1) && tm.valid;
+    // the swizzled TMA store needs a 1024-byte aligned source; otherwise plain stores
+    const bool use_tma = (NL == 1) && tm.valid && (smem_u32(S.stage) & 1023u) == 0;
 
     if (tid < 32) S.hist[tid] = 0;
     int cur_lat = -1;
@@ -734,9 +753,10 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapPa
         // rank base of this row: issued early, used after the barriers below
         uint32_t pre_row = 0, pre_lat = 0;
         if (rs && valid_row) {
-            const int64_t seg = L.seg0 + ((int64_t)(g.z0 + lz) * L.ny + (g.y0 + ly)) * L.nbx + g.bx;
-            pre_row = W.pre[seg];
-            pre_lat = W.pre[L.seg0];
+            // roots of the lattice's earlier rows, then of this row's earlier segments
+            const int64_t q = (int64_t)(g.z0 + lz) * L.ny + (g.y0 + ly);
+            pre_row = W.pre[L.row0 + q] + bytes_sum(W.cnt, L.seg0 + q * L.nbx, g.bx);
+            pre_lat = W.pre[L.row0];
         }
 
         if (use_tma && tid == 0) bulk_wait_read0();    // the previous tile's store has read S.stage
@@ -763,7 +783,7 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapPa
 
         // a4-a7: one pass over the runs of each row in x order: cluster roots get
         // their rank, size and histogram entry; every run writes its label
-        int64_t rank = (int64_t)pre_row - (int64_t)pre_lat;
+        int64_t rank = (int64_t)(uint32_t)(pre_row - pre_lat);
         const int site_row = ((g.z0 + lz) * L.ny + (g.y0 + ly)) * L.nx + g.x0;
         int h0 = 0, h1 = 0, h2 = 0, h3 = 0;   // histogram bins 0..3, combined per warp below
         uint32_t w = rs;
@@ -798,9 +818,10 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapPa
                 h3 += bin == 3;
                 if (bin >= 4) atomicAdd(&S.hist[bin], 1);
             }
-            const int len = run_len(m, x0);
-            int *dst = S.stage + r * 32 + x0;
-            for (int x = 0; x < len; ++x) dst[x] = lab;
+            const int xe = x0 + run_len(m, x0);
+            int *row = S.stage + r * 32;
+            const int sw = (r & 7) << 2;
+            for (int x = x0; x < xe; ++x) row[x ^ sw] = lab;
         }
         {
             const int s0 = (int)__reduce_add_sync(0xffffffffu, (unsigned)h0);
@@ -828,7 +849,7 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapPa
                 for (int rr = wid; rr < R; rr += NW) {
                     const int yy = rr % TY, zz = rr / TY;
                     if (yy <= g.lastY && zz <= g.lastZ)
-                        __stcs(out + (int64_t)zz * sxy + (int64_t)yy * L.nx, S.stage[rr * 32 + lane]);
+                        __stcs(out + (int64_t)zz * sxy + (int64_t)yy * L.nx, S.stage[stage_idx(rr, lane)]);
                 }
         }
     }
@@ -905,12 +926,12 @@ static cudaError_t launch_all(const LatDev *lats, int n, const Plan &P, const Wo
     mark(2);
     k_face_merge<TY, TZ, NL><<<(unsigned)((3 * P.ntiles + 7) / 8), 256, 0, st>>>(B, W, P.ntiles);
     mark(3);
-    k_piece_finalize<NL><<<(unsigned)P.ntiles, 256, 0, st>>>(B, W);
+    k_piece_finalize<NL><<<(unsigned)((P.ntiles + 7) / 8), 256, 0, st>>>(B, W, P.ntiles);
     mark(4);
-    const int64_t nb = (P.nseg + SCAN_CH) / SCAN_CH;   // covers index nseg (the total)
-    k_scan_reduce<<<(unsigned)nb, SCAN_NT, 0, st>>>(W.cnt, P.nseg, W.bsum);
+    const int64_t nb = (P.nrows + SCAN_CH) / SCAN_CH;   // covers index nrows (the total)
+    k_scan_reduce<NL><<<(unsigned)nb, SCAN_NT, 0, st>>>(B, W.cnt, P.nrows, W.bsum);
     k_scan_blocks<<<1, 1024, 0, st>>>(W.bsum, nb);
-    k_scan_apply<<<(unsigned)nb, SCAN_NT, 0, st>>>(W.cnt, P.nseg, W.bsum, W.pre);
+    k_scan_apply<NL><<<(unsigned)nb, SCAN_NT, 0, st>>>(B, W.cnt, P.nrows, W.bsum, W.pre);
     mark(5);
     k_lattice_finish<NL><<<(unsigned)n, 32, 0, st>>>(B, W);
     mark(6);

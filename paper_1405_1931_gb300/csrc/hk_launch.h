@@ -24,6 +24,7 @@ struct TileInfo {
 struct Plan {
     int64_t ntiles;      // tiles of all lattices in the launch
     int64_t nseg;        // row segments of all lattices
+    int64_t nrows;       // lattice rows (y, z) of all lattices
     int64_t piece_cap;   // ntiles * max_boundary
 };
 

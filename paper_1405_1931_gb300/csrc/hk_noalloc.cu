@@ -40,11 +40,11 @@ Carve carve(const hk::TileInfo &ti, const hk::Plan &P) {
     Carve c{};
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += a256(bytes); return o; };
-    const int64_t nb = (P.nseg + 4096) / 4096;
+    const int64_t nb = (P.nrows + 4096) / 4096;
     c.mask = take((size_t)P.ntiles * ti.rows * 4);
     c.codes = take((size_t)P.ntiles * ti.maxruns * 2);
-    c.cnt = take((size_t)P.nseg * 4);
-    c.pre = take((size_t)(P.nseg + 1) * 4);
+    c.cnt = take((size_t)P.nseg);
+    c.pre = take((size_t)(P.nrows + 1) * 4);
     c.bsum = take((size_t)nb * 4);
     c.face = take((size_t)P.ntiles * ti.face_stride * 2);
     c.tinfo = take((size_t)P.ntiles * 16);
@@ -71,10 +71,11 @@ extern "C" int hk_label_noalloc(const float *phi, int nx, int ny, int nz, const 
 
     hk::TileInfo ti;
     hk::tile_info(TY, TZ, ti);
-    hk::Plan P{0, 0, 0};
+    hk::Plan P{0, 0, 0, 0};
     const int64_t nbx = (nx + hk::TX - 1) / hk::TX, nby = (ny + TY - 1) / TY, nbz = (nz + TZ - 1) / TZ;
     P.ntiles = nbx * nby * nbz;
     P.nseg = nbx * (int64_t)ny * nz;
+    P.nrows = (int64_t)ny * nz;
     P.piece_cap = P.ntiles * ti.max_boundary;
     const Carve c = carve(ti, P);
     if (c.total > SCRATCH_BYTES) return HK_ERR_TOO_LARGE;   // rejected before touching the GPU
@@ -95,7 +96,7 @@ extern "C" int hk_label_noalloc(const float *phi, int nx, int ny, int nz, const 
     hk::Work W;
     W.mask = reinterpret_cast<uint32_t *>(base + c.mask);
     W.codes = reinterpret_cast<uint16_t *>(base + c.codes);
-    W.cnt = reinterpret_cast<uint32_t *>(base + c.cnt);
+    W.cnt = reinterpret_cast<uint8_t *>(base + c.cnt);
     W.pre = reinterpret_cast<uint32_t *>(base + c.pre);
     W.bsum = reinterpret_cast<uint32_t *>(base + c.bsum);
     W.face = reinterpret_cast<uint16_t *>(base + c.face);
@@ -127,6 +128,7 @@ extern "C" int hk_label_noalloc(const float *phi, int nx, int ny, int nz, const 
     d.nbx = (int)nbx; d.nby = (int)nby; d.nbz = (int)nbz;
     d.tile0 = 0;
     d.seg0 = 0;
+    d.row0 = 0;
 
     hk::TmapPair tm;
     std::memset(&tm, 0, sizeof(tm));   // plain-load path: no tensor maps
