@@ -15,6 +15,8 @@ scaling); only rank 0 runs the reference arm.
 from __future__ import annotations
 
 import argparse
+import glob
+import hashlib
 import json
 import os
 import subprocess
@@ -31,9 +33,9 @@ if ROOT not in sys.path:
 METRIC = "Gsites/s labelled+sized at 1024^3 p_c; batched vs per-lattice; p50/p99 latency"
 P_C = 0.3116
 L_HEADLINE = 1024
-# kernels of one hk_label call: occupancy, tile_label, face_merge, piece_finalize,
-# three scan kernels, lattice_finish, flatten
-LAUNCHES_PER_CALL = 9
+# kernels of one hk_label call: occupancy, tile_label (fast pass and the pass over
+# dense tiles), face_merge, piece_finalize, three scan kernels, lattice_finish, flatten
+LAUNCHES_PER_CALL = 10
 
 
 def parse():
@@ -56,6 +58,29 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per lattice site of one
+# hk_label call at p_c, per pass, from one ncu capture of a 512^3 call (the summary
+# with its command is profiles/hk_label_critical512_dram_traffic.md), scaled by the
+# number of sites.  It holds only for the kernel sources it was taken on, identified
+# by TRAFFIC_SOURCE_SHA; after any change to them it is reported as null.
+TRAFFIC_SITES = 512 ** 3
+TRAFFIC_BYTES = {"occupancy": 554.2e6, "tile_label": 63.7e6, "face_merge": 37.0e6, "piece_finalize": 29.9e6,
+                 "scan": 8.5e6, "lattice_finish": 0.0, "flatten": 628.7e6}
+TRAFFIC_SOURCE_SHA = "1c7ba12b58842588"
+
+
+def kernel_source_sha() -> str:
+    files = []
+    for ext in ("*.cu", "*.cuh", "*.h"):
+        files += glob.glob(os.path.join(ROOT, "paper_1405_1931_gb300", "csrc", ext))
+    h = hashlib.sha256()
+    for f in sorted(files):
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def read_peaks():
@@ -346,16 +371,19 @@ def main():
     path_bytes = 8 * N + 8 * n_clusters + 8 * 32
     path_achieved = path_bytes / (ms_step * 1e-3) / 1e9
     attributed = {"occupancy": 4 * N, "flatten": 4 * N + 8 * n_clusters + 8 * 32}
+    traffic_ok = kernel_source_sha() == TRAFFIC_SOURCE_SHA
     total_pass_ms = sum(passes)
     kernels = []
     for name, ms in zip(names, passes):
         b = attributed.get(name, 0)
         kernels.append({"kernel": name, "avg_ms": ms, "share": ms / total_pass_ms, "algorithmic_bytes": b,
                         "achieved_gbs": (b / (ms * 1e-3) / 1e9) if b else 0.0,
-                        "frac": (b / (ms * 1e-3) / 1e9 / peak) if b else 0.0})
+                        "frac": (b / (ms * 1e-3) / 1e9 / peak) if b else 0.0,
+                        "traffic": TRAFFIC_BYTES[name] * N / TRAFFIC_SITES if traffic_ok else None})
     dom = max(kernels, key=lambda k: k["avg_ms"])
+    path_traffic = sum(TRAFFIC_BYTES.values()) * N / TRAFFIC_SITES if traffic_ok else None
     roofline = {"bound": "hbm", "unit": "GB/s", "achieved": path_achieved, "peak": peak,
-                "frac": path_achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                "frac": path_achieved / peak, "traffic": path_traffic, "peak_kind": peak_kind,
                 "scope": "one hk_label call (all passes)", "algorithmic_bytes": path_bytes,
                 "dominant_kernel": dom["kernel"], "dominant_share": dom["share"]}
 

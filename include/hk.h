@@ -54,7 +54,7 @@ extern "C" {
 
 #define HK_OK            0
 #define HK_ERR_ARG       1  /* null pointer, dimension < 1, negative capacity, bad count */
-#define HK_ERR_TOO_LARGE 2  /* nx*ny*nz >= 2^31 */
+#define HK_ERR_TOO_LARGE 2  /* nx*ny*nz >= 2^31 (hk_label_noalloc: scratch too small) */
 #define HK_ERR_CAPACITY  3  /* more clusters than sizes_cap (labels, hist, count still valid) */
 #define HK_ERR_CUDA      4  /* a CUDA runtime call failed (see hk_last_cuda_error) */
 #define HK_ERR_TIMEOUT   5  /* a bounded device-side wait gave up */

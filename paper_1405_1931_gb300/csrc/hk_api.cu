@@ -562,7 +562,7 @@ const char *hk_strerror(int status) {
     switch (status) {
         case HK_OK: return "ok";
         case HK_ERR_ARG: return "invalid argument";
-        case HK_ERR_TOO_LARGE: return "lattice too large (nx*ny*nz >= 2^31)";
+        case HK_ERR_TOO_LARGE: return "lattice too large (nx*ny*nz >= 2^31, or beyond the allocation-free scratch)";
         case HK_ERR_CAPACITY: return "more clusters than sizes_cap";
         case HK_ERR_CUDA: return "CUDA runtime error";
         case HK_ERR_TIMEOUT: return "device-side wait timed out";
