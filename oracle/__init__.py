@@ -57,6 +57,11 @@ def _bind(lib):
     f.restype = ctypes.c_int
     f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+    g = lib.hk_oracle_interior
+    g.restype = ctypes.c_int
+    g.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                  ctypes.c_void_p]
     return lib
 
 
@@ -81,6 +86,38 @@ def label(phi: np.ndarray, periodic=(1, 1, 1), sizes_cap: int | None = None, lib
         raise RuntimeError(f"hk_oracle_label failed with status {rc}")
     k = int(ncl[0])
     return labels, sizes[:min(k, int(sizes_cap))].copy(), hist, k
+
+
+def interior(index: np.ndarray, periodic=(1, 1, 1), sizes_cap: int | None = None, lib=None):
+    """Interior/exterior identification of Sec. 6, steps 3-5, on an index field.
+
+    ``index`` is float32 (nz, ny, nx): I < -0.5 far from every membrane, I in
+    [-0.5, 0.5] near one (negative inside).  Returns ``(labels, sizes, hist,
+    n_clusters, inside)``: the labelling of the far sites (as ``label``) and
+    int8 ``inside[k]`` = 1 interior, 0 exterior, -1 undetermined, for each
+    cluster in label order.
+    """
+    lib = lib or load()
+    index = np.ascontiguousarray(index, dtype=np.float32)
+    if index.ndim != 3:
+        raise ValueError("index must have shape (nz, ny, nx)")
+    nz, ny, nx = index.shape
+    n = index.size
+    if sizes_cap is None:
+        sizes_cap = (n + 1) // 2
+    labels = np.empty(index.shape, dtype=np.int32)
+    sizes = np.zeros(max(int(sizes_cap), 1), dtype=np.int64)
+    inside = np.zeros(max(int(sizes_cap), 1), dtype=np.int8)
+    hist = np.zeros(32, dtype=np.int64)
+    ncl = np.zeros(1, dtype=np.int64)
+    per = np.array([int(bool(p)) for p in periodic], dtype=np.int32)
+    rc = lib.hk_oracle_interior(index.ctypes.data, nx, ny, nz, per.ctypes.data, labels.ctypes.data,
+                                sizes.ctypes.data, int(sizes_cap), hist.ctypes.data, ncl.ctypes.data,
+                                inside.ctypes.data)
+    if rc not in (OK, ERR_CAPACITY):
+        raise RuntimeError(f"hk_oracle_interior failed with status {rc}")
+    k = min(int(ncl[0]), int(sizes_cap))
+    return labels, sizes[:k].copy(), hist, int(ncl[0]), inside[:k].copy()
 
 
 def status(phi: np.ndarray, periodic=(1, 1, 1), sizes_cap: int = 0, lib=None) -> int:

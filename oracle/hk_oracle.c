@@ -47,6 +47,22 @@
  *                    (clusters ordered by their smallest site index).
  *   hist_out[b]    = number of clusters with floor(log2(size)) == b, b < 32.
  *   n_clusters_out = number of clusters.
+ *
+ * hk_oracle_interior follows the interior/exterior identification of Sec. 6
+ * (steps 3-5) on an index field I: sites far from every membrane keep
+ * I = I_0 < -0.5, sites within half a lattice constant of a membrane have
+ * -0.5 <= I <= 0.5, negative on the inner side and positive on the outer side
+ * (step 2).  Readings used:
+ *   - step 4: the clusters are those of the far sites, taken as I < -0.5,
+ *     labelled exactly as above (same labels, sizes, histogram, count);
+ *   - step 5 ("an interior cluster is surrounded by sites with negative I
+ *     while an exterior cluster borders on sites with positive I"): every
+ *     face-neighbour pair (cluster site, near site) votes with the sign of I at
+ *     the near site (I == 0 or NaN: no vote), along the six directions with
+ *     the same periodic wraps as the labelling; a cluster with more negative
+ *     votes is interior (1), with more positive votes exterior (0), otherwise
+ *     undetermined (-1).  inside_out[k] is the tag of the cluster with
+ *     compacted id k+1.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -62,6 +78,9 @@ int hk_oracle_label(const float *phi, int nx, int ny, int nz, const int periodic
                     int32_t *labels_out, int64_t *sizes_out, int64_t sizes_cap,
                     int64_t *hist_out, int64_t *n_clusters_out);
 int hk_oracle_version(void);
+int hk_oracle_interior(const float *index, int nx, int ny, int nz, const int periodic[3],
+                       int32_t *labels_out, int64_t *sizes_out, int64_t sizes_cap,
+                       int64_t *hist_out, int64_t *n_clusters_out, int8_t *inside_out);
 
 int hk_oracle_version(void) { return 1; }
 
@@ -209,4 +228,61 @@ int hk_oracle_label(const float *phi, int nx, int ny, int nz, const int periodic
 
     free(compact); free(count); free(t.lol); free(t.first);
     return (n > sizes_cap) ? HKO_ERR_CAPACITY : HKO_OK;
+}
+
+int hk_oracle_interior(const float *index, int nx, int ny, int nz, const int periodic[3],
+                       int32_t *labels_out, int64_t *sizes_out, int64_t sizes_cap,
+                       int64_t *hist_out, int64_t *n_clusters_out, int8_t *inside_out) {
+    if (!index || !periodic || !labels_out || !hist_out || !n_clusters_out) return HKO_ERR_ARG;
+    if (nx < 1 || ny < 1 || nz < 1 || sizes_cap < 0) return HKO_ERR_ARG;
+    if (sizes_cap > 0 && (!sizes_out || !inside_out)) return HKO_ERR_ARG;
+    const int64_t N = (int64_t)nx * ny * nz;
+    if (N >= ((int64_t)1 << 31)) return HKO_ERR_TOO_LARGE;
+
+    /* Step 4: the far sites (I < -0.5) are the occupied sites of the labelling. */
+    float *far = (float *)malloc((size_t)N * sizeof(float));
+    if (!far) return HKO_ERR_NOMEM;
+    for (int64_t s = 0; s < N; ++s) far[s] = (index[s] < -0.5f) ? 1.0f : -1.0f;
+    int rc = hk_oracle_label(far, nx, ny, nz, periodic, labels_out, sizes_out, sizes_cap, hist_out,
+                             n_clusters_out);
+    free(far);
+    if (rc != HKO_OK && rc != HKO_ERR_CAPACITY) return rc;
+    const int64_t n = *n_clusters_out;
+
+    /* Compacted id of every cluster, from its label (the cluster's first site):
+     * labels are ordered like the compacted ids. */
+    int32_t *rank = (int32_t *)malloc((size_t)N * sizeof(int32_t));
+    int64_t *votes = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+    if (!rank || !votes) { free(rank); free(votes); return HKO_ERR_NOMEM; }
+    int32_t next = 0;
+    for (int64_t s = 0; s < N; ++s) if (labels_out[s] == s) rank[s] = next++;
+
+    /* Step 5: each (cluster site, near site) face pair votes with the sign of I
+     * at the near site. */
+    const int dims[3] = {nx, ny, nz};
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const int64_t s = x + (int64_t)nx * (y + (int64_t)ny * z);
+                if (labels_out[s] >= 0) continue;          /* a cluster site, not a near site */
+                const float v = index[s];
+                const int sign = (v < 0.0f) ? -1 : (v > 0.0f) ? 1 : 0;
+                if (sign == 0) continue;
+                for (int axis = 0; axis < 3; ++axis)
+                    for (int d = -1; d <= 1; d += 2) {
+                        int c[3] = {x, y, z};
+                        c[axis] += d;
+                        if (c[axis] < 0 || c[axis] >= dims[axis]) {
+                            if (!periodic[axis]) continue;
+                            c[axis] = (c[axis] + dims[axis]) % dims[axis];
+                        }
+                        const int64_t m = c[0] + (int64_t)nx * (c[1] + (int64_t)ny * c[2]);
+                        if (labels_out[m] >= 0) votes[rank[labels_out[m]]] += sign;
+                    }
+            }
+    for (int64_t k = 0; k < n && k < sizes_cap; ++k)
+        inside_out[k] = (int8_t)(votes[k] < 0 ? 1 : votes[k] > 0 ? 0 : -1);
+    free(rank);
+    free(votes);
+    return rc;
 }

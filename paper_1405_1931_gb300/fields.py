@@ -155,6 +155,70 @@ def capsule_interior_count(L: int, semi_axes: tuple) -> int:
     return int(core.sum())
 
 
+INDEX_FAR = np.float32(-1.0)      # I_0 < -0.5: far from every membrane (Sec. 6, step 1)
+INDEX_INNER = np.float32(-0.25)   # near a membrane, inner side (Sec. 6, step 2: -d)
+INDEX_OUTER = np.float32(0.25)    # near a membrane, outer side (+d)
+
+
+def capsule_params(n: int, shape: tuple, seed: int, a_lo: float = 6.0, a_hi: float = 20.0, tries: int = 1000):
+    """Up to n non-overlapping ellipsoidal capsules inside a box of shape (nz, ny, nx).
+
+    Candidate j draws counters 6j..6j+5 of stream ``seed``: a centre uniform in
+    the box shrunk by the largest semi-axis + 3 on each side, and three semi-axes
+    uniform in [a_lo, a_hi].  A candidate is kept when its bounding sphere stays
+    3 sites clear of every kept one.  Returns a list of (centre_xyz, axes_xyz).
+    """
+    nz, ny, nx = shape
+    box = (nx, ny, nz)
+    kept = []
+    for j in range(tries):
+        if len(kept) == n:
+            break
+        u = uniform(seed, np.arange(6 * j, 6 * j + 6, dtype=np.uint64)).astype(np.float64)
+        axes = tuple(a_lo + (a_hi - a_lo) * u[3 + i] for i in range(3))
+        m = max(axes) + 3.0
+        if any(2 * m >= b for b in box):
+            continue
+        centre = tuple(m + (box[i] - 2 * m) * u[i] for i in range(3))
+        ok = all(np.linalg.norm(np.subtract(centre, c)) > m + max(a) + 3.0 for c, a in kept)
+        if ok:
+            kept.append((centre, axes))
+    return kept
+
+
+def capsule_index_field(shape: tuple, capsules) -> np.ndarray:
+    """Index field I of Sec. 6 (steps 1-2) for closed ellipsoidal membranes.
+
+    For capsule c, F_c(x) = sum_i ((x_i - c_i) / a_i)^2 (float64).  Sites with
+    F_c <= 1 and a 6-neighbour F_c > 1 form the inner layer (I = -0.25), sites
+    with F_c > 1 and a 6-neighbour F_c <= 1 the outer layer (I = +0.25); every
+    other site is far (I = -1).  The two layers close around each capsule, so
+    they separate its interior from the exterior.  Capsules must stay clear of
+    each other and of the box faces (``capsule_params`` ensures both).
+    """
+    nz, ny, nx = shape
+    I = np.full(shape, INDEX_FAR, dtype=np.float32)
+    z = np.arange(-1, nz + 1, dtype=np.float64)
+    y = np.arange(-1, ny + 1, dtype=np.float64)
+    x = np.arange(-1, nx + 1, dtype=np.float64)
+    nbs = ((slice(0, -2), slice(1, -1), slice(1, -1)), (slice(2, None), slice(1, -1), slice(1, -1)),
+           (slice(1, -1), slice(0, -2), slice(1, -1)), (slice(1, -1), slice(2, None), slice(1, -1)),
+           (slice(1, -1), slice(1, -1), slice(0, -2)), (slice(1, -1), slice(1, -1), slice(2, None)))
+    for (cx, cy, cz), (ax, ay, az) in capsules:
+        F = (((z - cz) / az) ** 2)[:, None, None] + (((y - cy) / ay) ** 2)[None, :, None] \
+            + (((x - cx) / ax) ** 2)[None, None, :]
+        inside = F <= 1.0
+        core = inside[1:-1, 1:-1, 1:-1]
+        any_out = np.zeros_like(core)
+        any_in = np.zeros_like(core)
+        for sl in nbs:
+            any_out |= ~inside[sl]
+            any_in |= inside[sl]
+        I[~core & any_in] = INDEX_OUTER
+        I[core & any_out] = INDEX_INNER
+    return I
+
+
 # ----------------------------------------------------------------------------------------------
 # Workload recipes (shapes, sizes and value distributions of the paper's use cases)
 # ----------------------------------------------------------------------------------------------

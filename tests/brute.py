@@ -132,3 +132,32 @@ def canonical_from_partition(part: np.ndarray):
     else:
         sizes = np.zeros(0, dtype=np.int64)
     return labels.reshape(part.shape).astype(np.int32), sizes, log2_hist(sizes), int(sizes.size)
+
+
+def interior_tags(index: np.ndarray, periodic):
+    """Sec. 6, step 5, from the definitions: clusters of the far sites (I < -0.5) by
+    BFS; every face pair (cluster site, near site) adds the sign of I at the near
+    site to its cluster (the six directions with the periodic wraps); a negative sum
+    is interior (1), a positive one exterior (0), zero undetermined (-1).  Returns
+    (labels, sizes, hist, n, tags) with clusters in order of their first site."""
+    occ = index < -0.5
+    labels, sizes, hist, n = bfs_label(occ, periodic)
+    nz, ny, nx = index.shape
+    dims = (nx, ny, nz)
+    roots = sorted({int(v) for v in labels.reshape(-1) if v >= 0})
+    order = {r: k for k, r in enumerate(roots)}
+    votes = [0] * len(roots)
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                if occ[z, y, x]:
+                    continue
+                v = float(index[z, y, x])
+                sign = -1 if v < 0 else (1 if v > 0 else 0)   # NaN compares false: no vote
+                if sign == 0:
+                    continue
+                for (ax, ay, az) in neighbours(x, y, z, dims, periodic):
+                    if occ[az, ay, ax]:
+                        votes[order[int(labels[az, ay, ax])]] += sign
+    tags = np.array([1 if v < 0 else (0 if v > 0 else -1) for v in votes], dtype=np.int8)
+    return labels, sizes, hist, n, tags

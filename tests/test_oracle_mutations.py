@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 import oracle
-from brute import bfs_label, log2_hist
+from brute import bfs_label, interior_tags, log2_hist
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "hk_oracle.c")
 
@@ -36,6 +36,14 @@ MUTATIONS = {
                       "if (c - 1 < sizes_cap) sizes_out[(c % n)] = size;"),
     "raster_y_stride": ("const int64_t sx = 1, sy = nx, sz = (int64_t)nx * ny;",
                         "const int64_t sx = 1, sy = ny, sz = (int64_t)nx * ny;"),
+    # interior/exterior identification (Sec. 6, steps 3-5)
+    "interior_vote_sign": ("const int sign = (v < 0.0f) ? -1 : (v > 0.0f) ? 1 : 0;",
+                           "const int sign = (v < 0.0f) ? 1 : (v > 0.0f) ? -1 : 0;"),
+    "interior_far_le": ("far[s] = (index[s] < -0.5f) ? 1.0f : -1.0f;", "far[s] = (index[s] <= -0.5f) ? 1.0f : -1.0f;"),
+    "interior_no_vote_wrap": ("if (!periodic[axis]) continue;", "continue;"),
+    "interior_tag_swapped": ("(int8_t)(votes[k] < 0 ? 1 : votes[k] > 0 ? 0 : -1)",
+                             "(int8_t)(votes[k] < 0 ? 1 : votes[k] > 0 ? 0 : 1)"),
+    "interior_vote_x_only": ("for (int axis = 0; axis < 3; ++axis)", "for (int axis = 0; axis < 1; ++axis)"),
 }
 
 
@@ -75,6 +83,16 @@ def battery(lib):
     got = lab(row, (0, 0, 0))
     assert got[1].tolist() == [1, 2, 3, 4]
     np.testing.assert_array_equal(got[2], log2_hist([1, 2, 3, 4]))
+    # interior/exterior tags against the brute-force votes
+    values = np.array([-1.0, -0.5, -0.25, 0.0, 0.25, np.nan], dtype=np.float32)
+    for it in range(40):
+        shape = tuple(int(v) for v in rng.integers(1, 6, size=3))
+        I = values[rng.choice(len(values), size=shape, p=[0.5, 0.05, 0.2, 0.05, 0.15, 0.05])]
+        per = pers[it % 8]
+        got = oracle.interior(I, per, lib=lib)
+        want = interior_tags(I, per)
+        same(got[:4], want[:4])
+        np.testing.assert_array_equal(got[4], want[4])
 
 
 def _build(tmp_path, name, mutation):
