@@ -98,6 +98,28 @@ int hk_label(hk_ctx *ctx, const float *phi, int nx, int ny, int nz, const int pe
              int32_t *labels_out, int64_t *sizes_out, int64_t sizes_cap,
              int64_t *hist_out, int64_t *n_clusters_out, void *stream);
 
+/* Interior and exterior of closed membranes (Sec. 6, steps 3-5).
+ *   index          device, float32[nz][ny][nx]: the index field I of Sec. 6, step 2:
+ *                  I < -0.5 far from every membrane (the initial I_0), -0.5 <= I <= 0.5
+ *                  near one, negative on its inner side and positive on its outer side.
+ *   inside_out     device, int8[sizes_cap] (may be NULL when sizes_cap == 0):
+ *                  inside_out[k] = 1 if the cluster with the (k+1)-th smallest label is
+ *                  interior, 0 if exterior, -1 if undetermined.
+ *   The other arguments are those of hk_label.
+ * The clusters are those of the far sites, I < -0.5 (step 4, with the labels,
+ * sizes, histogram and count of hk_label for that occupancy).  Step 5 decides
+ * a cluster by the signs of I around it: every face-neighbour pair (cluster
+ * site, near site), along the six directions with the same periodic wraps,
+ * votes with the sign of I at the near site (I == 0 and NaN do not vote); more
+ * negative votes -> interior, more positive -> exterior, a tie -> -1.
+ * Same stream and capacity rules as hk_label; the tags of clusters beyond
+ * sizes_cap are not written.  The workspace grows by 4 B per site/8 and 4 B per
+ * sizes_cap entry for the votes.
+ * Errors: HK_ERR_ARG, HK_ERR_TOO_LARGE, HK_ERR_NOMEM, HK_ERR_CUDA, HK_ERR_CAPACITY. */
+int hk_label_interior(hk_ctx *ctx, const float *index, int nx, int ny, int nz, const int periodic[3],
+                      int32_t *labels_out, int64_t *sizes_out, int64_t sizes_cap,
+                      int64_t *hist_out, int64_t *n_clusters_out, int8_t *inside_out, void *stream);
+
 /* One lattice of a batch: the arguments of hk_label bundled (device pointers,
  * same meaning and layout). */
 typedef struct hk_lattice {

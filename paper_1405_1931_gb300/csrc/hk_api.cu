@@ -53,10 +53,12 @@ constexpr int64_t MAX_SITES = (int64_t)1 << 31;
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t mask, codes, cnt, pre, bsum, face, tinfo, parent, key, psize, xcol, ovf, ncl, total;
+    size_t mask, codes, cnt, pre, bsum, face, tinfo, parent, key, psize, xcol, ovf, rootbits, votes, ncl, total;
 };
 
-Layout make_layout(const TileInfo &ti, const Plan &P) {
+// votes_cap > 0: also the root bits and the per-cluster votes of the interior/exterior
+// identification (index fields)
+Layout make_layout(const TileInfo &ti, const Plan &P, int64_t votes_cap = 0) {
     Layout L{};
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
@@ -73,6 +75,8 @@ Layout make_layout(const TileInfo &ti, const Plan &P) {
     L.psize = take((size_t)P.piece_cap * 4);
     L.xcol = take((size_t)P.ntiles * (ti.rows / 32) * 2 * 4);
     L.ovf = take((size_t)P.ntiles * 4);
+    L.rootbits = take(votes_cap > 0 ? (size_t)P.nseg * 4 : 0);
+    L.votes = take((size_t)votes_cap * 4);
     L.ncl = take((size_t)hk::MAX_LAT_PER_LAUNCH * 8);
     L.total = off;
     return L;
@@ -195,7 +199,11 @@ void fold_timing(hk_ctx *ctx, int slot) {
 }
 
 // Label lats[0..n) with at most MAX_LAT_PER_LAUNCH lattices per pass sequence.
-int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st) {
+// index_field (one lattice only): the lattice is an index field; label its far sites
+// (I < -0.5) and, when inside != nullptr, write the interior/exterior tags of its
+// clusters to inside.
+int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st, bool index_field = false,
+                 int8_t *inside = nullptr) {
     TileInfo ti;
     if (!hk::tile_info(ctx->ty, ctx->tz, ti)) return HK_ERR_ARG;
     for (int i = 0; i < n; ++i) {
@@ -232,7 +240,7 @@ int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st) {
         Plan P{0, 0, 0, 0};
         for (int i = chunk_start[c]; i < chunk_start[c + 1]; ++i) add_lattice(ti, lats[i].nx, lats[i].ny, lats[i].nz, P);
         P.piece_cap = P.ntiles * ti.max_boundary;
-        need = std::max(need, make_layout(ti, P).total);
+        need = std::max(need, make_layout(ti, P, inside ? lats[0].sizes_cap : 0).total);
     }
     int rc = ensure_ws(ctx, need);
     if (rc != HK_OK) return rc;
@@ -268,10 +276,12 @@ int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st) {
             d.tile0 = P.ntiles;
             d.seg0 = P.nseg;
             d.row0 = P.nrows;
+            d.occ_mode = index_field ? 1 : 0;
+            d.inside = inside;
             add_lattice(ti, l.nx, l.ny, l.nz, P);
         }
         P.piece_cap = P.ntiles * ti.max_boundary;
-        const Layout Ly = make_layout(ti, P);
+        const Layout Ly = make_layout(ti, P, inside ? lats[0].sizes_cap : 0);
         char *base = static_cast<char *>(ctx->ws);
         Work W;
         W.mask = reinterpret_cast<uint32_t *>(base + Ly.mask);
@@ -287,6 +297,8 @@ int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st) {
         W.xcol = reinterpret_cast<uint32_t *>(base + Ly.xcol);
         W.status = ctx->dstatus;
         W.ovf = reinterpret_cast<int32_t *>(base + Ly.ovf);
+        W.rootbits = inside ? reinterpret_cast<uint32_t *>(base + Ly.rootbits) : nullptr;
+        W.votes = inside ? reinterpret_cast<int32_t *>(base + Ly.votes) : nullptr;
         W.novf = ctx->dstatus + 1;
         W.piece_cap = P.piece_cap;
         int64_t *slots = reinterpret_cast<int64_t *>(base + Ly.ncl);
@@ -309,6 +321,10 @@ int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st) {
         else std::memset(&tm, 0, sizeof(tm));
         e = hk::launch_label(ctx->ty, ctx->tz, dev.data(), cn, P, W, tm, st, ev);
         if (e != cudaSuccess) return fail_cuda(ctx, e);
+        if (inside && dev[0].sizes_cap > 0) {
+            e = hk::launch_interior(dev[0], W, st);
+            if (e != cudaSuccess) return fail_cuda(ctx, e);
+        }
         if (chunk_check) {
             // the capacity rule needs the counts: wait for this chunk
             any_check = true;
@@ -389,6 +405,23 @@ int hk_label(hk_ctx *ctx, const float *phi, int nx, int ny, int nz, const int pe
     l.hist = hist_out;
     l.n_clusters = n_clusters_out;
     return run_lattices(ctx, &l, 1, static_cast<cudaStream_t>(stream));
+}
+
+int hk_label_interior(hk_ctx *ctx, const float *index, int nx, int ny, int nz, const int periodic[3],
+                      int32_t *labels_out, int64_t *sizes_out, int64_t sizes_cap, int64_t *hist_out,
+                      int64_t *n_clusters_out, int8_t *inside_out, void *stream) {
+    if (!ctx || !periodic) return HK_ERR_ARG;
+    if (sizes_cap > 0 && !inside_out) return HK_ERR_ARG;
+    hk_lattice l;
+    l.phi = index;
+    l.nx = nx; l.ny = ny; l.nz = nz;
+    for (int a = 0; a < 3; ++a) l.periodic[a] = periodic[a];
+    l.labels = labels_out;
+    l.sizes = sizes_out;
+    l.sizes_cap = sizes_cap;
+    l.hist = hist_out;
+    l.n_clusters = n_clusters_out;
+    return run_lattices(ctx, &l, 1, static_cast<cudaStream_t>(stream), true, sizes_cap > 0 ? inside_out : nullptr);
 }
 
 int hk_label_batched(hk_ctx *ctx, const hk_lattice *lats, int n, void *stream) {

@@ -42,7 +42,8 @@ struct LatDev {
     int nx, ny, nz;
     int per[3];
     int nbx, nby, nbz;
-    int pad_;
+    int occ_mode;    // 0: occupied iff phi > 0; 1: iff phi < -0.5 (far sites of an index field)
+    int8_t *inside;  // interior/exterior tag per cluster (index fields), or nullptr
     int64_t tile0;   // first global tile id
     int64_t seg0;    // first global segment id (row-major: ((z*ny + y)*nbx + bx))
     int64_t row0;    // first global row id (z*ny + y)
@@ -66,6 +67,8 @@ struct Work {
     uint32_t *xcol;     // [ntiles * 2 * R/32] occupancy of each tile's first (x = 0) and last
                         // (x = lastX) column, one bit per tile row
     int32_t *status;    // [1] device-side error flags (STATUS_*), owned by the context
+    uint32_t *rootbits; // [nseg] cluster-root run starts of each row segment (index fields only)
+    int32_t *votes;     // [sizes_cap] sign votes per cluster (index fields only)
     int32_t *ovf;       // [ntiles] tiles with more runs than the fast tile pass holds
     int32_t *novf;      // [1] entries of ovf (reset by the occupancy pass of every call)
     int64_t piece_cap;  // entries of parent/key/psize: bounds every union-find path
@@ -168,6 +171,10 @@ __device__ __forceinline__ TileGeo tile_geo(const LatDev &L, int64_t t) {
     g.wrapZ = L.per[2] && L.nbz == 1 && L.nz >= 2;
     return g;
 }
+
+// Occupancy of a site: phi > 0 (Sec. 2); for an index field (Sec. 6, step 4) the
+// sites far from every membrane, I < -0.5.  NaN is never occupied.
+__device__ __forceinline__ bool occupied(float v, int mode) { return mode ? (v < -0.5f) : (v > 0.0f); }
 
 __device__ __forceinline__ uint32_t run_starts(uint32_t m) { return m & ~(m << 1); }
 // bits 0..x set

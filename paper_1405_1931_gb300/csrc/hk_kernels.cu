@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(256) k_occupancy(const __grid_constant__ LatBa
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const uint32_t w = __ballot_sync(0xffffffffu, v[u] > 0.0f);
+                const uint32_t w = __ballot_sync(0xffffffffu, occupied(v[u], L.occ_mode));
                 if (lane == u0 + u) mine = w;
             }
         }
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(256) k_occupancy_tma(const __grid_constant__ T
             uint32_t mine = 0;
 #pragma unroll 8
             for (int j = 0; j < 32; ++j) {
-                const uint32_t w = __ballot_sync(0xffffffffu, S.buf[s][(r0 + j) * 32 + lane] > 0.0f);
+                const uint32_t w = __ballot_sync(0xffffffffu, occupied(S.buf[s][(r0 + j) * 32 + lane], L.occ_mode));
                 if (lane == j) mine = w;
             }
             W.mask[t * R + r0 + lane] = mine;
@@ -786,6 +786,7 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapPa
         int64_t rank = (int64_t)(uint32_t)(pre_row - pre_lat);
         const int site_row = ((g.z0 + lz) * L.ny + (g.y0 + ly)) * L.nx + g.x0;
         int h0 = 0, h1 = 0, h2 = 0, h3 = 0;   // histogram bins 0..3, combined per warp below
+        uint32_t rootbits = 0;                // first sites of cluster roots in this row
         uint32_t w = rs;
         int id = rb;
         while (w) {
@@ -811,6 +812,7 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapPa
             if (size > 0) {
                 if (rank < L.sizes_cap) L.sizes[rank] = size;
                 ++rank;
+                rootbits |= 1u << x0;
                 const int bin = 31 - __clz(size);
                 h0 += bin == 0;
                 h1 += bin == 1;
@@ -823,6 +825,8 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapPa
             const int sw = (r & 7) << 2;
             for (int x = x0; x < xe; ++x) row[x ^ sw] = lab;
         }
+        if (L.inside && ly <= g.lastY && lz <= g.lastZ)   // index fields: ranks of any root, later
+            W.rootbits[L.seg0 + ((int64_t)(g.z0 + lz) * L.ny + (g.y0 + ly)) * L.nbx + g.bx] = rootbits;
         {
             const int s0 = (int)__reduce_add_sync(0xffffffffu, (unsigned)h0);
             const int s1 = (int)__reduce_add_sync(0xffffffffu, (unsigned)h1);
@@ -857,6 +861,76 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapPa
     __syncthreads();
     if (cur_lat >= 0 && tid < 32 && S.hist[tid] && B.lat[cur_lat].hist)
         atomicAdd(reinterpret_cast<unsigned long long *>(B.lat[cur_lat].hist) + tid, (unsigned long long)S.hist[tid]);
+}
+
+// --------------------------------------------------------------------------------------
+// Interior/exterior identification (Sec. 6, step 5) for an index field labelled with
+// occ_mode 1: every face pair (cluster site, near site) votes with the sign of I at
+// the near site; a cluster with more negative votes is interior.  One lattice.
+// --------------------------------------------------------------------------------------
+// Rank (compacted id - 1) of the cluster whose first site is `lab`: roots of the
+// earlier rows, of the earlier segments of its row and of its segment before it.
+__device__ __forceinline__ int64_t rank_of_root(const LatDev &L, const Work &W, int lab) {
+    const int x = lab % L.nx, q = lab / L.nx;
+    const int64_t rowseg = L.seg0 + (int64_t)q * L.nbx;
+    return (int64_t)(uint32_t)(W.pre[L.row0 + q] - W.pre[L.row0]) + bytes_sum(W.cnt, rowseg, x >> 5) +
+           __popc(W.rootbits[rowseg + (x >> 5)] & ((1u << (x & 31)) - 1u));
+}
+
+__global__ void __launch_bounds__(256) k_votes_clear(const LatDev L, Work W) {
+    const int64_t n = *L.ncl < L.sizes_cap ? *L.ncl : L.sizes_cap;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        W.votes[k] = 0;
+}
+
+__global__ void __launch_bounds__(256) k_votes(const LatDev L, Work W) {
+    const int64_t N = (int64_t)L.nx * L.ny * L.nz;
+    const int dims[3] = {L.nx, L.ny, L.nz};
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+        const float v = L.phi[s];
+        if (!(v >= -0.5f)) continue;              // a cluster site (or NaN): not a near site
+        const int sign = v < 0.0f ? -1 : (v > 0.0f ? 1 : 0);
+        if (sign == 0) continue;
+        const int x = (int)(s % L.nx);
+        const int64_t q = s / L.nx;
+        const int y = (int)(q % L.ny), z = (int)(q / L.ny);
+#pragma unroll
+        for (int dir = 0; dir < 6; ++dir) {
+            const int axis = dir >> 1;
+            int c[3] = {x, y, z};
+            c[axis] += (dir & 1) ? 1 : -1;
+            if (c[axis] < 0 || c[axis] >= dims[axis]) {
+                if (!L.per[axis]) continue;
+                c[axis] = c[axis] < 0 ? dims[axis] - 1 : 0;
+            }
+            const int lab = L.labels[c[0] + (int64_t)L.nx * (c[1] + (int64_t)L.ny * c[2])];
+            if (lab < 0) continue;
+            const int64_t k = rank_of_root(L, W, lab);
+            if (k < L.sizes_cap) atomicAdd(W.votes + k, sign);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_inside(const LatDev L, Work W) {
+    const int64_t n = *L.ncl < L.sizes_cap ? *L.ncl : L.sizes_cap;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int v = W.votes[k];
+        L.inside[k] = (int8_t)(v < 0 ? 1 : (v > 0 ? 0 : -1));
+    }
+}
+
+cudaError_t launch_interior(const LatDev &L, const Work &W, cudaStream_t st) {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t N = (int64_t)L.nx * L.ny * L.nz;
+    int64_t gv = (N + 255) / 256;
+    if (gv > (int64_t)nsm * 16) gv = (int64_t)nsm * 16;
+    const unsigned gc = (unsigned)(nsm > 0 ? nsm * 4 : 1);
+    k_votes_clear<<<gc, 256, 0, st>>>(L, W);
+    k_votes<<<(unsigned)(gv > 0 ? gv : 1), 256, 0, st>>>(L, W);
+    k_inside<<<gc, 256, 0, st>>>(L, W);
+    return cudaGetLastError();
 }
 
 // --------------------------------------------------------------------------------------

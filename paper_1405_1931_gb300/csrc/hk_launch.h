@@ -38,4 +38,8 @@ bool tile_info(int ty, int tz, TileInfo &ti);
 cudaError_t launch_label(int ty, int tz, const LatDev *lats, int n, const Plan &P, const Work &W,
                          const TmapPair &tm, cudaStream_t st, cudaEvent_t *ev);
 
+// Interior/exterior tags of a lattice labelled with occ_mode 1 (after launch_label on
+// the same stream; needs W.rootbits and W.votes).
+cudaError_t launch_interior(const LatDev &L, const Work &W, cudaStream_t st);
+
 }  // namespace hk

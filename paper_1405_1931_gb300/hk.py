@@ -21,6 +21,7 @@ HK_ERR_CUDA, HK_ERR_TIMEOUT, HK_ERR_NOMEM = 4, 5, 6
 
 EXPORTED = ("hk_create", "hk_destroy", "hk_workspace_bytes", "hk_reserve", "hk_label", "hk_label_batched",
             "hk_label_host", "hk_set_tile", "hk_set_timing", "hk_get_timing", "hk_sync_status", "hk_set_graphs", "hk_last_cuda_error", "hk_strerror", "hk_label_noalloc",
+            "hk_label_interior",
             "hk_gen_iid", "hk_gen_spheres", "hk_gen_spheres_dev", "hk_gen_capsule")
 
 _lock = threading.Lock()
@@ -62,6 +63,7 @@ def load():
             "hk_label_batched": (I, [P, ctypes.POINTER(hk_lattice), I, P]),
             "hk_label_host": (I, [P, P, I, I, I, P, P, P, I64, P, P, P]),
             "hk_label_noalloc": (I, [P, I, I, I, P, P, P, I64, P, P, P]),
+            "hk_label_interior": (I, [P, P, I, I, I, P, P, P, I64, P, P, P, P]),
             "hk_set_tile": (I, [P, I, I]),
             "hk_set_timing": (I, [P, I]),
             "hk_set_graphs": (I, [P, I]),
@@ -112,6 +114,12 @@ def hk_label(ctx, phi, nx, ny, nz, periodic, labels_out, sizes_out, sizes_cap, h
              stream=0) -> int:
     return load().hk_label(ctx, phi, nx, ny, nz, _per(periodic), labels_out, sizes_out, int(sizes_cap),
                            hist_out, n_clusters_out, stream)
+
+
+def hk_label_interior(ctx, index, nx, ny, nz, periodic, labels_out, sizes_out, sizes_cap, hist_out, n_clusters_out,
+                      inside_out, stream=0) -> int:
+    return load().hk_label_interior(ctx, index, nx, ny, nz, _per(periodic), labels_out, sizes_out, int(sizes_cap),
+                                    hist_out, n_clusters_out, inside_out, stream)
 
 
 def hk_label_batched(ctx, lats, stream=0) -> int:
@@ -270,6 +278,22 @@ class Labeller:
         if check and rc != HK_OK:
             raise HKError(rc, "hk_label")
         return labels, sizes, hist, ncl
+
+    def label_interior(self, index, periodic=(1, 1, 1), out=None, sizes_cap=None, stream=None, check=True):
+        """Sec. 6, steps 3-5 on an index field; returns (labels, sizes, hist, ncl, inside)."""
+        import torch
+        if not (index.is_cuda and index.dtype == torch.float32 and index.dim() == 3 and index.is_contiguous()):
+            raise ValueError("index must be a contiguous float32 CUDA tensor of shape (nz, ny, nx)")
+        nz, ny, nx = index.shape
+        if out is None:
+            out = self.alloc_outputs(index.shape, index.device, sizes_cap)
+        labels, sizes, hist, ncl, cap = out
+        inside = torch.empty(max(cap, 1), dtype=torch.int8, device=index.device)
+        rc = hk_label_interior(self.ctx, index.data_ptr(), nx, ny, nz, periodic, labels.data_ptr(), sizes.data_ptr(),
+                               cap, hist.data_ptr(), ncl.data_ptr(), inside.data_ptr(), _stream_handle(stream))
+        if check and rc != HK_OK:
+            raise HKError(rc, "hk_label_interior")
+        return labels, sizes, hist, ncl, inside
 
     def label_batched(self, items, stream=None, check=True):
         """items: list of (phi, periodic, (labels, sizes, hist, ncl, cap)) with CUDA tensors."""
