@@ -208,7 +208,7 @@ def time_single(lab, phi, per, reps, flush=None):
 
 
 def extra_configs(args, peak):
-    """The other four workloads: 32^3, 256^3 emulsion, the uneven batch, the served stream."""
+    """The other workloads: 32^3, 256^3 emulsion, capsule interiors, the uneven batch, the served stream."""
     import torch
     from paper_1405_1931_gb300 import autotune, fields, hk, serve
     res = {}
@@ -233,6 +233,32 @@ def extra_configs(args, peak):
     ms, ncl = time_single(lab, phi, (1, 1, 1), 20, flush)
     line("emulsion256", L ** 3, ms, ncl, "256^3 emulsion, 600 droplets r in [5,15], periodic", "L2 flushed between reps")
     del phi
+
+    # interior/exterior of closed membranes (Sec. 6, steps 3-5): 256^3 index field, 24 capsules
+    shape = (256, 256, 256)
+    caps = fields.capsule_params(24, shape, seed=12, a_lo=8.0, a_hi=30.0)
+    index = torch.from_numpy(fields.capsule_index_field(shape, caps)).cuda()
+    out = lab.alloc_outputs(shape, index.device)
+    for _ in range(3):
+        res_i = lab.label_interior(index, (1, 1, 1), out=out)
+    ts = []
+    s0 = torch.cuda.current_stream()
+    for _ in range(20):
+        flush_l2(flush)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s0)
+        res_i = lab.label_interior(index, (1, 1, 1), out=out)
+        b.record(s0)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    ms = float(np.median(ts))
+    ncl = int(res_i[3].item())
+    tags = res_i[4][:ncl].cpu().numpy()
+    line("capsule_interior256", 256 ** 3, ms, ncl, f"256^3 index field, {len(caps)} capsules (Sec. 6 steps 3-5), periodic",
+         "L2 flushed between reps")
+    res["capsule_interior256"].update({"interior": int((tags == 1).sum()), "exterior": int((tags == 0).sum()),
+                                       "undetermined": int((tags == -1).sum())})
+    del index, out, res_i
 
     # uneven batch of 96 lattices: per-lattice launches vs one batched launch sequence
     params = fields.batch_params(96, master_seed=2)

@@ -883,7 +883,15 @@ __global__ void __launch_bounds__(256) k_votes_clear(const LatDev L, Work W) {
         W.votes[k] = 0;
 }
 
+// Votes into the first VOTE_SMEM ranks are summed per CTA in shared memory and
+// added to the global counters once per CTA (a few clusters, such as the exterior
+// fluid, collect most votes); higher ranks go straight to global memory.
+constexpr int VOTE_SMEM = 1024;
+
 __global__ void __launch_bounds__(256) k_votes(const LatDev L, Work W) {
+    __shared__ int sv[VOTE_SMEM];
+    for (int i = threadIdx.x; i < VOTE_SMEM; i += blockDim.x) sv[i] = 0;
+    __syncthreads();
     const int64_t N = (int64_t)L.nx * L.ny * L.nz;
     const int dims[3] = {L.nx, L.ny, L.nz};
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
@@ -906,9 +914,14 @@ __global__ void __launch_bounds__(256) k_votes(const LatDev L, Work W) {
             const int lab = L.labels[c[0] + (int64_t)L.nx * (c[1] + (int64_t)L.ny * c[2])];
             if (lab < 0) continue;
             const int64_t k = rank_of_root(L, W, lab);
-            if (k < L.sizes_cap) atomicAdd(W.votes + k, sign);
+            if (k >= L.sizes_cap) continue;
+            if (k < VOTE_SMEM) atomicAdd(&sv[k], sign);
+            else atomicAdd(W.votes + k, sign);
         }
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < VOTE_SMEM; i += blockDim.x)
+        if (sv[i]) atomicAdd(W.votes + i, sv[i]);
 }
 
 __global__ void __launch_bounds__(256) k_inside(const LatDev L, Work W) {
