@@ -34,7 +34,7 @@ OK, ERR_ARG, ERR_TOO_LARGE, ERR_CAPACITY, ERR_NOMEM = 0, 1, 2, 3, 6
 
 def build(src: str = _SRC, out: str = _LIB, extra: tuple = ()) -> str:
     """Compile the oracle with gcc (portable flags only: it runs on x86 and Arm)."""
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-Wall", "-Wextra", *extra, "-o", out, src]
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-Wall", "-Wextra", *extra, "-o", out, src, "-lm"]
     subprocess.run(cmd, check=True)
     return out
 
@@ -57,6 +57,9 @@ def _bind(lib):
     f.restype = ctypes.c_int
     f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+    h = lib.hk_oracle_rc_histogram
+    h.restype = ctypes.c_int
+    h.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
     g = lib.hk_oracle_interior
     g.restype = ctypes.c_int
     g.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
@@ -118,6 +121,24 @@ def interior(index: np.ndarray, periodic=(1, 1, 1), sizes_cap: int | None = None
         raise RuntimeError(f"hk_oracle_interior failed with status {rc}")
     k = min(int(ncl[0]), int(sizes_cap))
     return labels, sizes[:k].copy(), hist, int(ncl[0]), inside[:k].copy()
+
+
+def rc_histogram(sizes, edges, lib=None):
+    """Droplet-size histogram by R_c (Fig. 5) with ascending ``edges``; returns (hist, rc_sum).
+
+    hist has len(edges) + 1 bins: below the first edge, between consecutive
+    edges, and at or above the last one; rc_sum is the sum of R_c.
+    """
+    lib = lib or load()
+    sizes = np.ascontiguousarray(sizes, dtype=np.int64)
+    edges = np.ascontiguousarray(edges, dtype=np.float64)
+    hist = np.zeros(len(edges) + 1, dtype=np.int64)
+    rc = np.zeros(1, dtype=np.float64)
+    rc_ = lib.hk_oracle_rc_histogram(sizes.ctypes.data, int(sizes.size), edges.ctypes.data, int(edges.size),
+                                     hist.ctypes.data, rc.ctypes.data)
+    if rc_ != OK:
+        raise RuntimeError(f"hk_oracle_rc_histogram failed with status {rc_}")
+    return hist, float(rc[0])
 
 
 def status(phi: np.ndarray, periodic=(1, 1, 1), sizes_cap: int = 0, lib=None) -> int:

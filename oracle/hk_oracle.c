@@ -63,7 +63,16 @@
  *     votes is interior (1), with more positive votes exterior (0), otherwise
  *     undetermined (-1).  inside_out[k] is the tag of the cluster with
  *     compacted id k+1.
+ *
+ * hk_oracle_rc_histogram bins cluster sizes V by R_c, the radius of a sphere of
+ * volume V (Fig. 5 caption: (4 pi / 3) R_c^3 = V), with caller-given ascending
+ * edges e_0 < ... < e_{m-1}.  R_c >= e is decided as V >= t(e) with
+ * t(e) = ((e * e) * e) * (4 pi / 3) in double precision, so no cube root decides
+ * a bin.  hist[0] counts R_c < e_0, hist[b] (1 <= b < m) counts
+ * e_{b-1} <= R_c < e_b and hist[m] counts R_c >= e_{m-1}.  rc_sum = sum of
+ * cbrt(3 V / (4 pi)) over the clusters (for the mean droplet radius).
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -81,6 +90,8 @@ int hk_oracle_version(void);
 int hk_oracle_interior(const float *index, int nx, int ny, int nz, const int periodic[3],
                        int32_t *labels_out, int64_t *sizes_out, int64_t sizes_cap,
                        int64_t *hist_out, int64_t *n_clusters_out, int8_t *inside_out);
+int hk_oracle_rc_histogram(const int64_t *sizes, int64_t n, const double *edges, int n_edges,
+                           int64_t *hist_out, double *rc_sum_out);
 
 int hk_oracle_version(void) { return 1; }
 
@@ -285,4 +296,25 @@ int hk_oracle_interior(const float *index, int nx, int ny, int nz, const int per
     free(rank);
     free(votes);
     return rc;
+}
+
+int hk_oracle_rc_histogram(const int64_t *sizes, int64_t n, const double *edges, int n_edges,
+                           int64_t *hist_out, double *rc_sum_out) {
+    if ((n > 0 && !sizes) || !edges || n_edges < 1 || !hist_out || n < 0) return HKO_ERR_ARG;
+    for (int b = 1; b < n_edges; ++b) if (!(edges[b - 1] < edges[b])) return HKO_ERR_ARG;
+    const double four_thirds_pi = 4.0 * 3.14159265358979323846 / 3.0;
+    for (int b = 0; b <= n_edges; ++b) hist_out[b] = 0;
+    double rc_sum = 0.0;
+    for (int64_t k = 0; k < n; ++k) {
+        const double V = (double)sizes[k];
+        int bin = 0;                                   /* number of edges with R_c >= e */
+        for (int b = 0; b < n_edges; ++b) {
+            const double e = edges[b];
+            if (V >= ((e * e) * e) * four_thirds_pi) bin = b + 1;
+        }
+        hist_out[bin] += 1;
+        rc_sum += cbrt(V / four_thirds_pi);
+    }
+    if (rc_sum_out) *rc_sum_out = rc_sum;
+    return HKO_OK;
 }

@@ -44,6 +44,10 @@ MUTATIONS = {
     "interior_tag_swapped": ("(int8_t)(votes[k] < 0 ? 1 : votes[k] > 0 ? 0 : -1)",
                              "(int8_t)(votes[k] < 0 ? 1 : votes[k] > 0 ? 0 : 1)"),
     "interior_vote_x_only": ("for (int axis = 0; axis < 3; ++axis)", "for (int axis = 0; axis < 1; ++axis)"),
+    # droplet-size histogram by R_c (Fig. 5)
+    "rc_bin_shift": ("if (V >= ((e * e) * e) * four_thirds_pi) bin = b + 1;", "if (V >= ((e * e) * e) * four_thirds_pi) bin = b;"),
+    "rc_radius_not_cubed": ("if (V >= ((e * e) * e) * four_thirds_pi) bin = b + 1;",
+                            "if (V >= (e * e) * four_thirds_pi) bin = b + 1;"),
 }
 
 
@@ -93,6 +97,10 @@ def battery(lib):
         want = interior_tags(I, per)
         same(got[:4], want[:4])
         np.testing.assert_array_equal(got[4], want[4])
+    # droplet-size histogram by R_c: hand-worked example
+    h, rc_sum = oracle.rc_histogram([1, 8, 27, 1000], [0.5, 1.0, 2.0, 5.0, 10.0], lib=lib)
+    assert h.tolist() == [0, 1, 2, 0, 1, 0]
+    assert abs(rc_sum - 16 * (3 / (4 * np.pi)) ** (1 / 3)) < 1e-9
 
 
 def _build(tmp_path, name, mutation):
