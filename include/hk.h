@@ -191,6 +191,26 @@ int hk_label_noalloc(const float *phi, int nx, int ny, int nz, const int periodi
                      int32_t *labels_out, int64_t *sizes_out, int64_t sizes_cap,
                      int64_t *hist_out, int64_t *n_clusters_out, void *stream);
 
+/* Droplet-size histogram by R_c, the radius of a sphere with the cluster's
+ * volume (Fig. 5 caption: (4 pi / 3) R_c^3 = V), over caller-given bin edges.
+ *   sizes       device, int64[sizes_cap]: cluster sizes (e.g. hk_label's sizes_out).
+ *   n_clusters  device, int64[1]: the count; min(*n_clusters, sizes_cap) sizes are read.
+ *   edges       host, double[n_edges], strictly ascending, 1 <= n_edges <= 64; copied.
+ *   hist_out    device, int64[n_edges + 1]: [0] counts R_c < edges[0], [b] counts
+ *               edges[b-1] <= R_c < edges[b], [n_edges] counts R_c >= edges[n_edges-1].
+ *   rc_sum_out  device, double[1] or NULL: the sum of R_c (mean droplet radius =
+ *               rc_sum / count).
+ *   accumulate  0: the outputs are cleared first; nonzero: added to (the stacked
+ *               histograms of several realisations, Fig. 5).
+ * R_c >= e is decided as V >= ((e*e)*e)*(4 pi/3) in double precision (thresholds
+ * computed on the host), so no cube root decides a bin; rc_sum uses cbrt and is
+ * summed in an unspecified order.  Asynchronous on `stream`.
+ * Errors: HK_ERR_ARG (bad pointers, edges not ascending, n_edges out of range),
+ * HK_ERR_CUDA. */
+int hk_rc_histogram(const int64_t *sizes, const int64_t *n_clusters, int64_t sizes_cap,
+                    const double *edges, int n_edges, int64_t *hist_out, double *rc_sum_out,
+                    int accumulate, void *stream);
+
 /* Select the tile shape (rows per tile along y and z; x tiles are always 32
  * sites wide).  Supported: (ty, tz) in {(8,8), (16,8), (16,16), (32,8)}; 0,0 =
  * the library default.  Applies to later calls on this context.

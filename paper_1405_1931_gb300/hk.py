@@ -21,7 +21,7 @@ HK_ERR_CUDA, HK_ERR_TIMEOUT, HK_ERR_NOMEM = 4, 5, 6
 
 EXPORTED = ("hk_create", "hk_destroy", "hk_workspace_bytes", "hk_reserve", "hk_label", "hk_label_batched",
             "hk_label_host", "hk_set_tile", "hk_set_timing", "hk_get_timing", "hk_sync_status", "hk_set_graphs", "hk_last_cuda_error", "hk_strerror", "hk_label_noalloc",
-            "hk_label_interior",
+            "hk_label_interior", "hk_rc_histogram",
             "hk_gen_iid", "hk_gen_spheres", "hk_gen_spheres_dev", "hk_gen_capsule")
 
 _lock = threading.Lock()
@@ -64,6 +64,7 @@ def load():
             "hk_label_host": (I, [P, P, I, I, I, P, P, P, I64, P, P, P]),
             "hk_label_noalloc": (I, [P, I, I, I, P, P, P, I64, P, P, P]),
             "hk_label_interior": (I, [P, P, I, I, I, P, P, P, I64, P, P, P, P]),
+            "hk_rc_histogram": (I, [P, P, I64, P, I, P, P, I, P]),
             "hk_set_tile": (I, [P, I, I]),
             "hk_set_timing": (I, [P, I]),
             "hk_set_graphs": (I, [P, I]),
@@ -120,6 +121,27 @@ def hk_label_interior(ctx, index, nx, ny, nz, periodic, labels_out, sizes_out, s
                       inside_out, stream=0) -> int:
     return load().hk_label_interior(ctx, index, nx, ny, nz, _per(periodic), labels_out, sizes_out, int(sizes_cap),
                                     hist_out, n_clusters_out, inside_out, stream)
+
+
+def hk_rc_histogram(sizes, n_clusters, sizes_cap, edges, hist_out, rc_sum_out, accumulate=False, stream=0) -> int:
+    e = (ctypes.c_double * len(edges))(*[float(v) for v in edges])
+    return load().hk_rc_histogram(sizes, n_clusters, int(sizes_cap), e, len(edges), hist_out, rc_sum_out,
+                                  int(bool(accumulate)), stream)
+
+
+def rc_histogram(sizes, ncl, edges, cap=None, out=None, accumulate=False, stream=None):
+    """Droplet-size histogram by R_c on device tensors (hk_rc_histogram); returns (hist, rc_sum)."""
+    import torch
+    if out is None:
+        out = (torch.zeros(len(edges) + 1, dtype=torch.int64, device=sizes.device),
+               torch.zeros(1, dtype=torch.float64, device=sizes.device))
+    hist, rc_sum = out
+    cap = sizes.numel() if cap is None else int(cap)
+    rc = hk_rc_histogram(sizes.data_ptr(), ncl.data_ptr(), cap, edges, hist.data_ptr(), rc_sum.data_ptr(),
+                         accumulate, _stream_handle(stream))
+    if rc != HK_OK:
+        raise HKError(rc, "hk_rc_histogram")
+    return hist, rc_sum
 
 
 def hk_label_batched(ctx, lats, stream=0) -> int:
