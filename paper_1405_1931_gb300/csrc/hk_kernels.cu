@@ -785,7 +785,7 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapPa
         // their rank, size and histogram entry; every run writes its label
         int64_t rank = (int64_t)(uint32_t)(pre_row - pre_lat);
         const int site_row = ((g.z0 + lz) * L.ny + (g.y0 + ly)) * L.nx + g.x0;
-        int h0 = 0, h1 = 0, h2 = 0, h3 = 0;   // histogram bins 0..3, combined per warp below
+        const int site_row0 = (g.z0 * L.ny + g.y0) * L.nx + g.x0, sxy_i = L.nx * L.ny;
         uint32_t rootbits = 0;                // first sites of cluster roots in this row
         uint32_t w = rs;
         int id = rb;
@@ -793,52 +793,36 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapPa
             const int x0 = __ffs(w) - 1;
             w &= w - 1;
             const int c = S.code[id++];
-            int lab, size = -1;
-            if (c & CODE_BOUNDARY) {
-                const int k = c & CODE_LOW;
-                if (k < FlatSmem<TY, TZ>::GL) {
-                    lab = S.gl[k];
-                    if (c & CODE_ROOT) size = S.gsize[k];
-                } else {
-                    lab = __ldg(W.key + base + k);
-                    if (c & CODE_ROOT) size = __ldg(W.psize + base + k);
-                }
-            } else if (c & CODE_ROOT) {
-                lab = site_row + x0;
-                size = c & CODE_LOW;
-            } else {
-                lab = site_of<TY, TZ>(g, L, c);
+            const int k = c & CODE_LOW;
+            const bool isb = (c & CODE_BOUNDARY) != 0, isr = (c & CODE_ROOT) != 0;
+            const int kk = k < FlatSmem<TY, TZ>::GL ? k : 0;
+            int gl = S.gl[kk], gs = S.gsize[kk];
+            if (isb && k >= FlatSmem<TY, TZ>::GL) {
+                gl = __ldg(W.key + base + k);
+                gs = __ldg(W.psize + base + k);
             }
+            // all three labels are formed and one is selected (no divergent branches)
+            const int ci = (isb || isr) ? 0 : c;   // an interior non-root run: its root's position
+            const int crow = ci >> 5;
+            const int own = site_row + x0;
+            const int other = site_row0 + (crow / TY) * sxy_i + (crow % TY) * L.nx + (ci & 31);
+            const int lab = isb ? gl : (isr ? own : other);
+            const int size = isr ? (isb ? gs : k) : -1;
             if (size > 0) {
                 if (rank < L.sizes_cap) L.sizes[rank] = size;
                 ++rank;
                 rootbits |= 1u << x0;
-                const int bin = 31 - __clz(size);
-                h0 += bin == 0;
-                h1 += bin == 1;
-                h2 += bin == 2;
-                h3 += bin == 3;
-                if (bin >= 4) atomicAdd(&S.hist[bin], 1);
+                atomicAdd(&S.hist[31 - __clz(size)], 1);
             }
             const int xe = x0 + run_len(m, x0);
             int *row = S.stage + r * 32;
             const int sw = (r & 7) << 2;
-            for (int x = x0; x < xe; ++x) row[x ^ sw] = lab;
+            row[x0 ^ sw] = lab;
+#pragma unroll 1
+            for (int x = x0 + 1; x < xe; ++x) row[x ^ sw] = lab;
         }
         if (L.inside && ly <= g.lastY && lz <= g.lastZ)   // index fields: ranks of any root, later
             W.rootbits[L.seg0 + ((int64_t)(g.z0 + lz) * L.ny + (g.y0 + ly)) * L.nbx + g.bx] = rootbits;
-        {
-            const int s0 = (int)__reduce_add_sync(0xffffffffu, (unsigned)h0);
-            const int s1 = (int)__reduce_add_sync(0xffffffffu, (unsigned)h1);
-            const int s2 = (int)__reduce_add_sync(0xffffffffu, (unsigned)h2);
-            const int s3 = (int)__reduce_add_sync(0xffffffffu, (unsigned)h3);
-            if (lane == 0) {
-                if (s0) atomicAdd(&S.hist[0], s0);
-                if (s1) atomicAdd(&S.hist[1], s1);
-                if (s2) atomicAdd(&S.hist[2], s2);
-                if (s3) atomicAdd(&S.hist[3], s3);
-            }
-        }
         if (use_tma) fence_proxy_async();
         __syncthreads();
         if (use_tma) {
