@@ -348,8 +348,7 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
                 const int root = S.par[id];
                 if (root == id) S.par[id] = ROOTPOS | (r << 5) | x0;   // only this thread reads it
                 ++id;
-                const uint32_t bits = len == 32 ? 0xffffffffu : (((1u << len) - 1u) << x0);
-                const bool touch = (bits & conn) != 0;
+                const bool touch = ((conn >> x0) << (32 - len)) != 0;   // a connected site in the run
                 if (root != cur) {
                     atomicAdd(&S.aux[cur], acc);
                     cur = root;
