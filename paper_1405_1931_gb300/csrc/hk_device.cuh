@@ -384,13 +384,47 @@ __device__ __forceinline__ int g_find_ro(const int32_t *parent, int x, int64_t c
     return x;
 }
 
+// The finds of a and b with path halving, walked in lockstep so that the loads of
+// both chains are in flight together.
+__device__ __forceinline__ void g_find_pair(int32_t *parent, int &a, int &b, int64_t cap, int32_t *status) {
+    int pa = __ldcg(parent + a), pb = __ldcg(parent + b);
+    for (int64_t it = 0; pa != a || pb != b; ++it) {
+        if (it > cap) { atomicOr(status, STATUS_GLOBAL_LOOP); return; }
+        const bool ma = pa != a, mb = pb != b;       // chains not yet at a root
+        const int ga = ma ? __ldcg(parent + pa) : a;
+        const int gb = mb ? __ldcg(parent + pb) : b;
+        bool la = false, lb = false;                 // parent of the new a / b still to load
+        if (ma) {
+            if (ga == pa) {
+                a = pa;                              // pa is a root
+                pa = a;
+            } else {
+                __stcg(parent + a, ga);              // path halving: ga is an ancestor of a
+                a = ga;
+                la = true;
+            }
+        }
+        if (mb) {
+            if (gb == pb) {
+                b = pb;
+                pb = b;
+            } else {
+                __stcg(parent + b, gb);
+                b = gb;
+                lb = true;
+            }
+        }
+        if (la) pa = __ldcg(parent + a);
+        if (lb) pb = __ldcg(parent + b);
+    }
+}
+
 // A failed CAS means b was linked meanwhile, which lowers the key of b's root;
 // keys are distinct, so at most `cap` retries.
 __device__ __forceinline__ void g_union(int32_t *parent, const int32_t *key, int a, int b, int64_t cap,
                                         int32_t *status) {
     for (int64_t it = 0; it <= cap; ++it) {
-        a = g_find(parent, a, cap, status);
-        b = g_find(parent, b, cap, status);
+        g_find_pair(parent, a, b, cap, status);
         if (a == b) return;
         if (__ldg(key + b) < __ldg(key + a)) { int t = a; a = b; b = t; }
         if (atomicCAS(parent + b, b, a) == b) return;
