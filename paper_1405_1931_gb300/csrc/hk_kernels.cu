@@ -542,40 +542,73 @@ k_face_merge(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
 template <int NL>
 __global__ void __launch_bounds__(256)
 k_piece_finalize(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
+    __shared__ int hot_target[8];   // per warp: the cluster root its pieces fed most, and the sum
+    __shared__ int hot_sum[8];
     const int64_t t = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (t >= ntiles) return;
-    const int4 ti = W.tinfo[t];
-    if (ti.y == 0) return;
-    const LatDev &L = B.lat[(NL == 1) ? 0 : find_lattice(B.lat, B.n, t)];
-    for (int j0 = 0; j0 < ti.y; j0 += 32) {
-        const int j = j0 + lane;
-        const bool valid = j < ti.y;
-        const int pid = ti.x + j;
-        int root = -1, add = 0;
-        if (valid) {
-            root = g_find_ro(W.parent, pid, W.piece_cap, W.status);
-            if (root != pid) {
-                __stcg(W.parent + pid, root);
-                add = W.psize[pid];
-                // from here on key[pid] is the cluster's label and psize[pid] < 0 marks a
-                // non-root; only roots' keys are read by other threads, and a root's key
-                // never changes
-                W.key[pid] = __ldcg(W.key + root);
-                W.psize[pid] = -1;
-            } else {
-                const int k = W.key[pid];
-                const int q = k / L.nx, x = k - q * L.nx;
-                const int y = q % L.ny, z = q / L.ny;
-                const int64_t seg = L.seg0 + ((int64_t)z * L.ny + y) * L.nbx + (x >> 5);
-                // one byte per segment (at most 16 roots): add to it inside its aligned word
-                atomicAdd(reinterpret_cast<unsigned int *>(W.cnt + (seg & ~(int64_t)3)), 1u << (8 * (int)(seg & 3)));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // The root that collects most sizes (the percolating cluster's, above all) is added
+    // once per warp and then once per CTA; other roots once per group of lanes.
+    int hot = -1, hot_acc = 0;
+    const int4 ti = t < ntiles ? W.tinfo[t] : make_int4(0, 0, 0, 0);
+    if (ti.y > 0) {
+        const LatDev &L = B.lat[(NL == 1) ? 0 : find_lattice(B.lat, B.n, t)];
+        for (int j0 = 0; j0 < ti.y; j0 += 32) {
+            const int j = j0 + lane;
+            const bool valid = j < ti.y;
+            const int pid = ti.x + j;
+            int root = -1, add = 0;
+            if (valid) {
+                root = g_find_ro(W.parent, pid, W.piece_cap, W.status);
+                if (root != pid) {
+                    __stcg(W.parent + pid, root);
+                    add = W.psize[pid];
+                    // from here on key[pid] is the cluster's label and psize[pid] < 0 marks a
+                    // non-root; only roots' keys are read by other threads, and a root's key
+                    // never changes
+                    W.key[pid] = __ldcg(W.key + root);
+                    W.psize[pid] = -1;
+                } else {
+                    const int k = W.key[pid];
+                    const int q = k / L.nx, x = k - q * L.nx;          // q = z * ny + y
+                    const int64_t seg = L.seg0 + (int64_t)q * L.nbx + (x >> 5);
+                    // one byte per segment (at most 16 roots): add to it inside its aligned word
+                    atomicAdd(reinterpret_cast<unsigned int *>(W.cnt + (seg & ~(int64_t)3)),
+                              1u << (8 * (int)(seg & 3)));
+                }
+            }
+            const int target = (valid && root != pid) ? root : -1;
+            const unsigned peers = __match_any_sync(0xffffffffu, target);
+            const int sum = (int)__reduce_add_sync(peers, (unsigned)add);
+            const bool leader = target >= 0 && lane == __ffs(peers) - 1;
+            if (hot < 0) {   // warp-uniform: the first chunk names the warp's hot root (its largest group)
+                const unsigned key = leader ? ((unsigned)__popc(peers) << 5) | (unsigned)lane : 0u;
+                const unsigned best = __reduce_max_sync(0xffffffffu, key);
+                if (best) hot = __shfl_sync(0xffffffffu, target, (int)(best & 31u));
+            }
+            if (leader) {
+                if (target == hot) hot_acc += sum;
+                else atomicAdd(W.psize + target, sum);
             }
         }
-        const int target = (valid && root != pid) ? root : -1;
-        const unsigned peers = __match_any_sync(0xffffffffu, target);
-        const int sum = (int)__reduce_add_sync(peers, (unsigned)add);
-        if (target >= 0 && lane == __ffs(peers) - 1) atomicAdd(W.psize + target, sum);
+    }
+    hot_acc = (int)__reduce_add_sync(0xffffffffu, (unsigned)hot_acc);
+    if (lane == 0) {
+        hot_target[wid] = hot;
+        hot_sum[wid] = hot_acc;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {   // one add per distinct hot root of the CTA
+        const int h = hot_target[threadIdx.x];
+        if (h >= 0) {
+            bool first = true;
+            int s = 0;
+            for (int w = 0; w < 8; ++w)
+                if (hot_target[w] == h) {
+                    if (w < (int)threadIdx.x) first = false;
+                    s += hot_sum[w];
+                }
+            if (first) atomicAdd(W.psize + h, s);
+        }
     }
 }
 
