@@ -156,6 +156,21 @@ def cpu_baseline_oracle(side: int = 512, reps: int = 3):
             "sample": f"{reps} x {side}^3 iid phi at p=0.3116, periodic xyz (serial C oracle, {dt:.1f} s)"}
 
 
+def max_over_ranks(value: float, dist=None, device="cuda") -> float:
+    """The maximum of a per-rank number over all ranks (the value itself for one process)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gsites_per_s(world: int, sites_per_rank: int, ms_per_step: float) -> float:
+    """Whole-job throughput: each of the `world` ranks labels its own lattice every step."""
+    return world * sites_per_rank / (ms_per_step * 1e-3) / 1e9
+
+
 def run_reference(args, rank, world):
     """Reference arm: the CPU oracle as it stands, timed per step on a bounded sample."""
     if rank != 0:
@@ -376,12 +391,8 @@ def main():
     passes = hk.hk_get_timing(lab.ctx)
     hk.hk_set_timing(lab.ctx, False)
 
-    ms_step = ms_total / args.steps
-    if dist is not None:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = world * N / (ms_step * 1e-3) / 1e9
+    ms_step = max_over_ranks(ms_total / args.steps, dist)
+    value = job_gsites_per_s(world, N, ms_step)
 
     labels, sizes, hist, ncl, cap = out
     n_clusters = int(ncl.item())
@@ -436,13 +447,9 @@ def main():
         for _ in range(k_e2e):
             e2e_step()
         barrier()
-        ms_e2e = (time.perf_counter() - t0) / k_e2e * 1e3
-        if dist is not None:
-            t = torch.tensor([ms_e2e], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_e2e = float(t.item())
+        ms_e2e = max_over_ranks((time.perf_counter() - t0) / k_e2e * 1e3, dist)
         assert int(ncl_h[0]) == n_clusters
-        e2e = {"value": world * N / (ms_e2e * 1e-3) / 1e9, "unit": "Gsites/s", "ms_per_step": ms_e2e,
+        e2e = {"value": job_gsites_per_s(world, N, ms_e2e), "unit": "Gsites/s", "ms_per_step": ms_e2e,
                "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 4 * N + 8 * n_clusters + 8 * 32 + 8,
                "entry": "hk_label_host (pinned host buffers)"}
         del phi_h, lab_h, sizes_h
