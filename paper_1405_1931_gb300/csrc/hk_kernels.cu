@@ -36,7 +36,7 @@ struct LatBatch {
 // as medium.
 // --------------------------------------------------------------------------------------
 template <int TY, int TZ, int NL>
-__global__ void __launch_bounds__(256) k_occupancy(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
+__global__ void __launch_bounds__(256, 4) k_occupancy(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
     using SH = TileShape<TY, TZ>;
     constexpr int R = SH::R, U = 16;
     const int lane = threadIdx.x & 31;
@@ -49,21 +49,49 @@ __global__ void __launch_bounds__(256) k_occupancy(const __grid_constant__ LatBa
     const float *base = L.phi + (int64_t)g.z0 * sxy + (int64_t)g.y0 * L.nx + g.x0 + lane;
     const bool xin = lane <= g.lastX;
     uint32_t *out = W.mask + t * R;
+    // Whole 128-byte rows at 16-byte aligned addresses: lane l loads 4 sites (x = 4 (l % 8)
+    // .. + 3) of row l / 8 of each group of 4 rows, and the 8 lanes of a row OR their
+    // nibbles into the row's word.
+    const bool vec = g.lastX == TX - 1 && (L.nx & 3) == 0 && (reinterpret_cast<uintptr_t>(L.phi) & 15) == 0;
+    const int x4 = (lane & 7) * 4;
+    const float *base4 = L.phi + (int64_t)g.z0 * sxy + (int64_t)g.y0 * L.nx + g.x0 + x4;
     for (int r0 = 0; r0 < R; r0 += 32) {        // lane j keeps the word of row r0 + j
         uint32_t mine = 0;
+        if (vec) {
+            float4 v[8];
 #pragma unroll
-        for (int u0 = 0; u0 < 32; u0 += U) {
-            float v[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int rr = r0 + u0 + u, ly = rr % TY, lz = rr / TY;
-                v[u] = (xin && ly <= g.lastY && lz <= g.lastZ)
-                           ? __ldcs(base + (int64_t)lz * sxy + (int64_t)ly * L.nx) : 0.0f;
+            for (int q = 0; q < 8; ++q) {
+                const int rr = r0 + 4 * q + (lane >> 3), ly = rr % TY, lz = rr / TY;
+                v[q] = (ly <= g.lastY && lz <= g.lastZ)
+                           ? __ldcs(reinterpret_cast<const float4 *>(base4 + (int64_t)lz * sxy + (int64_t)ly * L.nx))
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
             }
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const uint32_t w = __ballot_sync(0xffffffffu, occupied(v[u], L.occ_mode));
-                if (lane == u0 + u) mine = w;
+            for (int q = 0; q < 8; ++q) {
+                uint32_t w = ((uint32_t)occupied(v[q].x, L.occ_mode) | ((uint32_t)occupied(v[q].y, L.occ_mode) << 1) |
+                              ((uint32_t)occupied(v[q].z, L.occ_mode) << 2) | ((uint32_t)occupied(v[q].w, L.occ_mode) << 3))
+                             << x4;
+                w |= __shfl_xor_sync(0xffffffffu, w, 1);
+                w |= __shfl_xor_sync(0xffffffffu, w, 2);
+                w |= __shfl_xor_sync(0xffffffffu, w, 4);
+                const uint32_t wq = __shfl_sync(0xffffffffu, w, (lane & 3) * 8);   // row r0 + 4 q + (lane & 3)
+                if ((lane >> 2) == q) mine = wq;
+            }
+        } else {
+#pragma unroll
+            for (int u0 = 0; u0 < 32; u0 += U) {
+                float v[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int rr = r0 + u0 + u, ly = rr % TY, lz = rr / TY;
+                    v[u] = (xin && ly <= g.lastY && lz <= g.lastZ)
+                               ? __ldcs(base + (int64_t)lz * sxy + (int64_t)ly * L.nx) : 0.0f;
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const uint32_t w = __ballot_sync(0xffffffffu, occupied(v[u], L.occ_mode));
+                    if (lane == u0 + u) mine = w;
+                }
             }
         }
         out[r0 + lane] = mine;
@@ -861,6 +889,18 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapPa
             if (tid == 0) {
                 tma_store_3d(&tm.labels, S.stage, g.x0, g.y0, g.z0);
                 bulk_commit();
+            }
+        } else if (g.lastX == TX - 1 && (L.nx & 3) == 0 && (reinterpret_cast<uintptr_t>(L.labels) & 15) == 0) {
+            // whole rows at 16-byte aligned addresses: lane l stores 4 labels (x = 4 (l % 8)
+            // .. + 3) of row l / 8 of each group of 4 rows (the swizzle keeps them together)
+            const int64_t sxy = (int64_t)L.nx * L.ny;
+            const int x4 = (lane & 7) * 4;
+            int32_t *out = L.labels + (int64_t)g.z0 * sxy + (int64_t)g.y0 * L.nx + g.x0 + x4;
+            for (int r4 = wid * 4; r4 < R; r4 += NW * 4) {
+                const int rr = r4 + (lane >> 3), yy = rr % TY, zz = rr / TY;
+                if (yy <= g.lastY && zz <= g.lastZ)
+                    __stcs(reinterpret_cast<int4 *>(out + (int64_t)zz * sxy + (int64_t)yy * L.nx),
+                           *reinterpret_cast<const int4 *>(S.stage + rr * 32 + (x4 ^ ((rr & 7) << 2))));
             }
         } else {
             const int64_t sxy = (int64_t)L.nx * L.ny;
