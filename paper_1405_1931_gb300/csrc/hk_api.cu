@@ -316,10 +316,9 @@ int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st, bo
             ev = ctx->ev[slot];
             ctx->ncalls += 1;
         }
-        hk::TmapPair tm;
-        if (cn == 1) make_tmaps(lats[c0], ctx->ty, ctx->tz, tm);
-        else std::memset(&tm, 0, sizeof(tm));
-        e = hk::launch_label(ctx->ty, ctx->tz, dev.data(), cn, P, W, tm, st, ev);
+        std::vector<hk::TmapPair> tms(cn);
+        for (int i = 0; i < cn; ++i) make_tmaps(lats[c0 + i], ctx->ty, ctx->tz, tms[i]);
+        e = hk::launch_label(ctx->ty, ctx->tz, dev.data(), cn, P, W, tms.data(), st, ev);
         if (e != cudaSuccess) return fail_cuda(ctx, e);
         if (inside && dev[0].sizes_cap > 0) {
             e = hk::launch_interior(dev[0], W, st);

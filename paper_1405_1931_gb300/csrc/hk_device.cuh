@@ -82,6 +82,13 @@ struct TmapPair {
     int valid;
 };
 
+// The tensor maps of every lattice of a launch (kernel parameters, so graphs keep them
+// by value).
+template <int NL>
+struct TmapBatch {
+    TmapPair tm[NL];
+};
+
 // A union-find path longer than the number of its nodes means corrupted
 // parents, and a TMA wait that never completes means a lost copy; every loop
 // below is capped, and on reaching the cap it records one of these flags and

@@ -17,6 +17,8 @@
 //   K4 flatten        persistent: decode the run codes, write the labels
 //                     (staged in shared memory, TMA tensor stores), the sizes
 //                     in label order and the histogram.
+#include <cstring>
+
 #include "hk_device.cuh"
 #include "hk_launch.h"
 
@@ -105,8 +107,8 @@ __global__ void __launch_bounds__(256, 4) k_occupancy(const __grid_constant__ La
     }
 }
 
-// K0 with TMA (single lattice, 16-byte aligned rows): persistent, a ring of two
-// tile buffers per CTA filled by cp.async.bulk.tensor loads completed on
+// K0 with TMA (every lattice of the launch with 16-byte aligned rows): persistent, a
+// ring of two tile buffers per CTA filled by cp.async.bulk.tensor loads completed on
 // mbarriers; while one tile is converted the next is in flight.
 template <int TY, int TZ>
 struct OccSmem {
@@ -115,15 +117,14 @@ struct OccSmem {
     uint64_t bar[2];
 };
 
-template <int TY, int TZ>
-__global__ void __launch_bounds__(256) k_occupancy_tma(const __grid_constant__ TmapPair tm, const __grid_constant__ LatBatch<1> B,
-                                                       Work W, int64_t ntiles) {
+template <int TY, int TZ, int NL>
+__global__ void __launch_bounds__(256) k_occupancy_tma(const __grid_constant__ TmapBatch<NL> TB,
+                                                       const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
     using SH = TileShape<TY, TZ>;
     constexpr int R = SH::R;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     OccSmem<TY, TZ> &S = *reinterpret_cast<OccSmem<TY, TZ> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const LatDev &L = B.lat[0];
     if (blockIdx.x == 0 && tid == 0) *W.novf = 0;           // the tile pass appends after this pass
     if (tid == 0) {
         mbar_init(&S.bar[0], 1);
@@ -132,10 +133,11 @@ __global__ void __launch_bounds__(256) k_occupancy_tma(const __grid_constant__ T
     }
     __syncthreads();
     auto issue = [&](int64_t t, int s) {
-        const TileGeo g = tile_geo<TY, TZ>(L, t);
+        const int lat = (NL == 1) ? 0 : find_lattice(B.lat, B.n, t);
+        const TileGeo g = tile_geo<TY, TZ>(B.lat[lat], t);
         fence_proxy_async();
         mbar_arrive_expect_tx(&S.bar[s], SH::SITES * 4);
-        tma_load_3d(S.buf[s], &tm.phi, &S.bar[s], g.x0, g.y0, g.z0);
+        tma_load_3d(S.buf[s], &TB.tm[lat].phi, &S.bar[s], g.x0, g.y0, g.z0);
     };
     const int64_t t0 = blockIdx.x, step = gridDim.x;
     if (tid == 0) {
@@ -149,6 +151,8 @@ __global__ void __launch_bounds__(256) k_occupancy_tma(const __grid_constant__ T
             if (tid == 0) atomicOr(W.status, STATUS_TMA_TIMEOUT);
             return;
         }
+        const LatDev &L = B.lat[(NL == 1) ? 0 : find_lattice(B.lat, B.n, t)];
+        const int lastX = tile_geo<TY, TZ>(L, t).lastX;
         // warp w converts rows [32 w', 32 w' + 32) in turns; lane j keeps row 32 w' + j
         for (int r0 = wid * 32; r0 < R; r0 += 32 * (256 / 32)) {
             uint32_t mine = 0;
@@ -158,7 +162,6 @@ __global__ void __launch_bounds__(256) k_occupancy_tma(const __grid_constant__ T
                 if (lane == j) mine = w;
             }
             W.mask[t * R + r0 + lane] = mine;
-            const int lastX = min(TX, L.nx - (int)((uint32_t)t % (uint32_t)L.nbx) * TX) - 1;
             const uint32_t c0 = __ballot_sync(0xffffffffu, mine & 1u);
             const uint32_t cl = __ballot_sync(0xffffffffu, (mine >> lastX) & 1u);
             if (lane == 0) {
@@ -789,14 +792,14 @@ __device__ __forceinline__ int site_of(const TileGeo &g, const LatDev &L, int po
 
 template <int TY, int TZ, int NL>
 __global__ void __launch_bounds__(TY * TZ, 1280 / (TY * TZ))
-k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapPair tm, Work W, int64_t ntiles) {
+k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapBatch<NL> TB, Work W, int64_t ntiles) {
     using SH = TileShape<TY, TZ>;
     constexpr int R = SH::R, NT = SH::NT, NW = NT / 32, MR = SH::MAXRUNS;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     FlatSmem<TY, TZ> &S = *reinterpret_cast<FlatSmem<TY, TZ> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     // the swizzled TMA store needs a 1024-byte aligned source; otherwise plain stores
-    const bool use_tma = (NL == 1) && tm.valid && (smem_u32(S.stage) & 1023u) == 0;
+    const bool stage_ok = (smem_u32(S.stage) & 1023u) == 0;
 
     if (tid < 32) S.hist[tid] = 0;
     int cur_lat = -1;
@@ -804,6 +807,7 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapPa
         const int lat = (NL == 1) ? 0 : find_lattice(B.lat, B.n, t);
         const LatDev &L = B.lat[lat];
         const TileGeo g = tile_geo<TY, TZ>(L, t);
+        const bool use_tma = TB.tm[lat].valid && stage_ok;
         const int4 ti = W.tinfo[t];
         const int base = ti.x, nb = ti.y, total = ti.z;
         const int r = tid, ly = r % TY, lz = r / TY;
@@ -819,7 +823,7 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapPa
             pre_lat = W.pre[L.row0];
         }
 
-        if (use_tma && tid == 0) bulk_wait_read0();    // the previous tile's store has read S.stage
+        if (tid == 0) bulk_wait_read0();               // a previous tile's store has read S.stage
         __syncthreads();
         if (lat != cur_lat) {                          // uniform: flush the histogram per lattice
             if (cur_lat >= 0 && tid < 32 && S.hist[tid] && B.lat[cur_lat].hist)
@@ -887,7 +891,7 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapPa
         __syncthreads();
         if (use_tma) {
             if (tid == 0) {
-                tma_store_3d(&tm.labels, S.stage, g.x0, g.y0, g.z0);
+                tma_store_3d(&TB.tm[lat].labels, S.stage, g.x0, g.y0, g.z0);
                 bulk_commit();
             }
         } else if (g.lastX == TX - 1 && (L.nx & 3) == 0 && (reinterpret_cast<uintptr_t>(L.labels) & 15) == 0) {
@@ -913,7 +917,7 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapPa
                 }
         }
     }
-    if (use_tma && tid == 0) bulk_wait0();
+    if (tid == 0) bulk_wait0();
     __syncthreads();
     if (cur_lat >= 0 && tid < 32 && S.hist[tid] && B.lat[cur_lat].hist)
         atomicAdd(reinterpret_cast<unsigned long long *>(B.lat[cur_lat].hist) + tid, (unsigned long long)S.hist[tid]);
@@ -1017,13 +1021,21 @@ static int persistent_grid(K kernel, int threads, size_t smem, int64_t ntiles) {
 }
 
 template <int TY, int TZ, int NL>
-static cudaError_t launch_all(const LatDev *lats, int n, const Plan &P, const Work &W, const TmapPair &tm,
+static cudaError_t launch_all(const LatDev *lats, int n, const Plan &P, const Work &W, const TmapPair *tms,
                               cudaStream_t st, cudaEvent_t *ev) {
     using SH = TileShape<TY, TZ>;
     LatBatch<NL> B;
     B.n = n;
     B.pad_ = 0;
     for (int i = 0; i < n; ++i) B.lat[i] = lats[i];
+    // tensor maps: the TMA occupancy pass needs every lattice's; flatten picks per tile
+    TmapBatch<NL> TB;
+    std::memset(&TB, 0, sizeof(TB));
+    bool all_tma = n > 0 && tms != nullptr;
+    for (int i = 0; i < n; ++i) {
+        if (tms) TB.tm[i] = tms[i];
+        all_tma = all_tma && TB.tm[i].valid;
+    }
     constexpr int CAP1 = LabelCfg<TY, TZ, true>::CAP, CAP1B = LabelCfg<TY, TZ, false>::CAP;
     const size_t smem1 = sizeof(LabelSmem<TY, TZ, CAP1>), smem1b = sizeof(LabelSmem<TY, TZ, CAP1B>);
     const size_t smem4 = sizeof(FlatSmem<TY, TZ>);
@@ -1044,20 +1056,17 @@ static cudaError_t launch_all(const LatDev *lats, int n, const Plan &P, const Wo
     const unsigned g4 = (unsigned)(P.ntiles < grid4 ? P.ntiles : grid4);
     auto mark = [&](int i) { if (ev) cudaEventRecord(ev[i], st); };
     mark(0);
-    if constexpr (NL == 1) {
-        if (tm.valid) {
-            static int grid0 = 0;
-            const size_t smem0 = sizeof(OccSmem<TY, TZ>);
-            if (!grid0) {
-                e = cudaFuncSetAttribute(k_occupancy_tma<TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem0);
-                if (e != cudaSuccess) return e;
-                grid0 = persistent_grid(k_occupancy_tma<TY, TZ>, 256, smem0, INT32_MAX);
-            }
-            const unsigned g0 = (unsigned)(P.ntiles < grid0 ? P.ntiles : grid0);
-            k_occupancy_tma<TY, TZ><<<g0, 256, smem0, st>>>(tm, B, W, P.ntiles);
-        } else {
-            k_occupancy<TY, TZ, NL><<<(unsigned)((P.ntiles + 7) / 8), 256, 0, st>>>(B, W, P.ntiles);
+    if (all_tma) {
+        static int grid0 = 0;
+        const size_t smem0 = sizeof(OccSmem<TY, TZ>);
+        if (!grid0) {
+            e = cudaFuncSetAttribute(k_occupancy_tma<TY, TZ, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem0);
+            if (e != cudaSuccess) return e;
+            grid0 = persistent_grid(k_occupancy_tma<TY, TZ, NL>, 256, smem0, INT32_MAX);
         }
+        const unsigned g0 = (unsigned)(P.ntiles < grid0 ? P.ntiles : grid0);
+        k_occupancy_tma<TY, TZ, NL><<<g0, 256, smem0, st>>>(TB, B, W, P.ntiles);
     } else {
         k_occupancy<TY, TZ, NL><<<(unsigned)((P.ntiles + 7) / 8), 256, 0, st>>>(B, W, P.ntiles);
     }
@@ -1078,16 +1087,16 @@ static cudaError_t launch_all(const LatDev *lats, int n, const Plan &P, const Wo
     mark(5);
     k_lattice_finish<NL><<<(unsigned)n, 32, 0, st>>>(B, W);
     mark(6);
-    k_flatten<TY, TZ, NL><<<g4, SH::NT, smem4, st>>>(B, tm, W, P.ntiles);
+    k_flatten<TY, TZ, NL><<<g4, SH::NT, smem4, st>>>(B, TB, W, P.ntiles);
     mark(7);
     return cudaGetLastError();
 }
 
 template <int TY, int TZ>
-static cudaError_t launch_shape(const LatDev *lats, int n, const Plan &P, const Work &W, const TmapPair &tm,
+static cudaError_t launch_shape(const LatDev *lats, int n, const Plan &P, const Work &W, const TmapPair *tms,
                                 cudaStream_t st, cudaEvent_t *ev) {
-    if (n == 1) return launch_all<TY, TZ, 1>(lats, n, P, W, tm, st, ev);
-    return launch_all<TY, TZ, MAX_LAT_PER_LAUNCH>(lats, n, P, W, tm, st, ev);
+    if (n == 1) return launch_all<TY, TZ, 1>(lats, n, P, W, tms, st, ev);
+    return launch_all<TY, TZ, MAX_LAT_PER_LAUNCH>(lats, n, P, W, tms, st, ev);
 }
 
 template <int TY, int TZ>
@@ -1109,12 +1118,12 @@ bool tile_info(int ty, int tz, TileInfo &ti) {
     return false;
 }
 
-cudaError_t launch_label(int ty, int tz, const LatDev *lats, int n, const Plan &P, const Work &W, const TmapPair &tm,
+cudaError_t launch_label(int ty, int tz, const LatDev *lats, int n, const Plan &P, const Work &W, const TmapPair *tms,
                          cudaStream_t st, cudaEvent_t *ev) {
-    if (ty == 8 && tz == 8) return launch_shape<8, 8>(lats, n, P, W, tm, st, ev);
-    if (ty == 16 && tz == 8) return launch_shape<16, 8>(lats, n, P, W, tm, st, ev);
-    if (ty == 16 && tz == 16) return launch_shape<16, 16>(lats, n, P, W, tm, st, ev);
-    if (ty == 32 && tz == 8) return launch_shape<32, 8>(lats, n, P, W, tm, st, ev);
+    if (ty == 8 && tz == 8) return launch_shape<8, 8>(lats, n, P, W, tms, st, ev);
+    if (ty == 16 && tz == 8) return launch_shape<16, 8>(lats, n, P, W, tms, st, ev);
+    if (ty == 16 && tz == 16) return launch_shape<16, 16>(lats, n, P, W, tms, st, ev);
+    if (ty == 32 && tz == 8) return launch_shape<32, 8>(lats, n, P, W, tms, st, ev);
     return cudaErrorInvalidValue;
 }
 

@@ -11,7 +11,9 @@ struct LatDev;
 struct Work;
 struct TmapPair;
 
-constexpr int MAX_LAT_PER_LAUNCH = 128;
+// lattices per launch: the descriptors and tensor maps of a launch travel as kernel
+// parameters (under the 32 KB parameter limit)
+constexpr int MAX_LAT_PER_LAUNCH = 64;
 
 struct TileInfo {
     int ty, tz;
@@ -32,11 +34,11 @@ constexpr int NUM_PASSES = 7;   // occupancy, tile_label, face_merge, piece_fina
 
 bool tile_info(int ty, int tz, TileInfo &ti);
 
-// ev: NUM_PASSES + 1 events recorded around the passes, or nullptr.  tm: tensor
-// maps for the single-lattice TMA path (tm->valid == 0 selects the cp.async /
-// plain-store path).
+// ev: NUM_PASSES + 1 events recorded around the passes, or nullptr.  tms: the tensor
+// maps of each of the n lattices (valid == 0: that lattice takes the plain-load and
+// plain-store paths), or nullptr for none.
 cudaError_t launch_label(int ty, int tz, const LatDev *lats, int n, const Plan &P, const Work &W,
-                         const TmapPair &tm, cudaStream_t st, cudaEvent_t *ev);
+                         const TmapPair *tms, cudaStream_t st, cudaEvent_t *ev);
 
 // Interior/exterior tags of a lattice labelled with occ_mode 1 (after launch_label on
 // the same stream; needs W.rootbits and W.votes).

@@ -134,7 +134,7 @@ extern "C" int hk_label_noalloc(const float *phi, int nx, int ny, int nz, const 
 
     hk::TmapPair tm;
     std::memset(&tm, 0, sizeof(tm));   // plain-load path: no tensor maps
-    e = hk::launch_label(TY, TZ, &d, 1, P, W, tm, st, nullptr);
+    e = hk::launch_label(TY, TZ, &d, 1, P, W, &tm, st, nullptr);
     if (e != cudaSuccess) return HK_ERR_CUDA;
 
     if (d.sizes_cap < (N + 1) / 2) {
