@@ -535,34 +535,84 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
 }
 
 // --------------------------------------------------------------------------------------
-// K2: face merge.  One warp per (tile, axis): the tile's low face list along the
-// axis is joined entry by entry with the high face list of its lower neighbour (for
-// tile 0 of a periodic axis: the last tile, the wrap).
+// K2: face merge.  One warp per tile: its low face lists along x, y and z are joined
+// entry by entry with the high face lists of its lower neighbours (for tile 0 of a
+// periodic axis: the last tile, the wrap).  Each lane takes U entries at a time and
+// walks the finds of all their endpoints in lockstep, so their loads are in flight
+// together; the roots are then linked by CAS, and a lost CAS falls back to g_union.
 // --------------------------------------------------------------------------------------
 template <int TY, int TZ, int NL>
 __global__ void __launch_bounds__(256)
 k_face_merge(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
     using SH = TileShape<TY, TZ>;
+    constexpr int U = 2, C = 2 * U;   // unions and chains per lane and step
     const int lane = threadIdx.x & 31;
-    const int64_t item = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (item >= 3 * ntiles) return;
-    const int64_t t = item / 3;
-    const int axis = (int)(item - 3 * t);
+    const int64_t t = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (t >= ntiles) return;
     const LatDev &L = B.lat[(NL == 1) ? 0 : find_lattice(B.lat, B.n, t)];
     const TileGeo g = tile_geo<TY, TZ>(L, t);
-    if (!(axis == 0 ? g.extXlo : axis == 1 ? g.extYlo : g.extZlo)) return;
     const int64_t plane = (int64_t)L.nbx * L.nby;
-    const int64_t nb = axis == 0 ? (g.bx > 0 ? t - 1 : t + (L.nbx - 1))
-                     : axis == 1 ? (g.by > 0 ? t - L.nbx : t + (int64_t)(L.nby - 1) * L.nbx)
-                                 : (g.bz > 0 ? t - plane : t + (int64_t)(L.nbz - 1) * plane);
+    const int64_t nbr[3] = {g.bx > 0 ? t - 1 : t + (L.nbx - 1),
+                            g.by > 0 ? t - L.nbx : t + (int64_t)(L.nby - 1) * L.nbx,
+                            g.bz > 0 ? t - plane : t + (int64_t)(L.nbz - 1) * plane};
     const uint16_t *F = W.face + t * SH::FACE_STRIDE;
-    const uint16_t *G = W.face + nb * SH::FACE_STRIDE;
-    const int n = F[SH::OFF_CNT + 2 * axis];
-    const int lo = axis == 0 ? SH::OFF_LX : axis == 1 ? SH::OFF_LY : SH::OFF_LZ;
-    const int hi = axis == 0 ? SH::OFF_HX : axis == 1 ? SH::OFF_HY : SH::OFF_HZ;
-    const int base = W.tinfo[t].x, bbase = W.tinfo[nb].x;
-    for (int i = lane; i < n; i += 32)
-        g_union(W.parent, W.key, base + F[lo + i], bbase + G[hi + i], W.piece_cap, W.status);
+    const int n0 = g.extXlo ? F[SH::OFF_CNT + 0] : 0;
+    const int n1 = g.extYlo ? F[SH::OFF_CNT + 2] : 0;
+    const int n2 = g.extZlo ? F[SH::OFF_CNT + 4] : 0;
+    const int total = n0 + n1 + n2;
+    const int64_t base = t * SH::MAX_BOUNDARY;   // each tile owns a fixed slice of the piece table
+    for (int i0 = 0; i0 < total; i0 += 32 * U) {
+        int x[C], p[C];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * 32 + lane;
+            if (i < total) {
+                const int axis = i < n0 ? 0 : (i < n0 + n1 ? 1 : 2);
+                const int j = i - (axis == 0 ? 0 : (axis == 1 ? n0 : n0 + n1));
+                const int lo = axis == 0 ? SH::OFF_LX : axis == 1 ? SH::OFF_LY : SH::OFF_LZ;
+                const int hi = axis == 0 ? SH::OFF_HX : axis == 1 ? SH::OFF_HY : SH::OFF_HZ;
+                const int64_t nb = nbr[axis];
+                x[2 * u] = (int)(base + F[lo + j]);
+                x[2 * u + 1] = (int)(nb * SH::MAX_BOUNDARY + W.face[nb * SH::FACE_STRIDE + hi + j]);
+            } else {
+                x[2 * u] = x[2 * u + 1] = -1;   // no entry
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c) p[c] = x[c] >= 0 ? __ldcg(W.parent + x[c]) : x[c];
+        // finds with path halving, all chains one step per round
+        for (int64_t it = 0;; ++it) {
+            bool moving = false;
+#pragma unroll
+            for (int c = 0; c < C; ++c) moving |= p[c] != x[c];
+            if (!moving) break;
+            if (it > W.piece_cap) { atomicOr(W.status, STATUS_GLOBAL_LOOP); break; }
+            int gp[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) gp[c] = p[c] != x[c] ? __ldcg(W.parent + p[c]) : x[c];
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                if (p[c] == x[c]) continue;
+                if (gp[c] == p[c]) {
+                    x[c] = p[c];                      // p is a root
+                } else {
+                    __stcg(W.parent + x[c], gp[c]);   // path halving: gp is an ancestor of x
+                    x[c] = gp[c];
+                    p[c] = -2;                        // to reload
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < C; ++c) p[c] = p[c] == -2 ? __ldcg(W.parent + x[c]) : (p[c] == x[c] || x[c] < 0 ? x[c] : p[c]);
+        }
+        // link the roots: the root with the larger key under the one with the smaller key
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            int a = x[2 * u], b = x[2 * u + 1];
+            if (a < 0 || a == b) continue;
+            if (__ldg(W.key + b) < __ldg(W.key + a)) { const int tmp = a; a = b; b = tmp; }
+            if (atomicCAS(W.parent + b, b, a) != b) g_union(W.parent, W.key, a, b, W.piece_cap, W.status);
+        }
+    }
 }
 
 // --------------------------------------------------------------------------------------
@@ -1076,7 +1126,7 @@ static cudaError_t launch_all(const LatDev *lats, int n, const Plan &P, const Wo
     k_tile_label<TY, TZ, NL, false><<<(unsigned)(P.ntiles < grid1b ? P.ntiles : grid1b), SH::NT, smem1b, st>>>(
         B, W, P.ntiles);
     mark(2);
-    k_face_merge<TY, TZ, NL><<<(unsigned)((3 * P.ntiles + 7) / 8), 256, 0, st>>>(B, W, P.ntiles);
+    k_face_merge<TY, TZ, NL><<<(unsigned)((P.ntiles + 7) / 8), 256, 0, st>>>(B, W, P.ntiles);
     mark(3);
     k_piece_finalize<NL><<<(unsigned)((P.ntiles + 7) / 8), 256, 0, st>>>(B, W, P.ntiles);
     mark(4);
