@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--size", type=int, default=L_HEADLINE, help="lattice side (default 1024)")
     ap.add_argument("--tile", default="", help="ty,tz tile override")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-streams", type=int, default=3,
+                    help="contexts (each on its own stream) that take alternate steps in the end-to-end run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="headline config only")
     ap.add_argument("--served-requests", type=int, default=2000)
@@ -424,35 +426,70 @@ def main():
                 "scope": "one hk_label call (all passes)", "algorithmic_bytes": path_bytes,
                 "dominant_kernel": dom["kernel"], "dominant_share": dom["share"]}
 
-    # end to end through the host-buffer entry point (copies inside the timed region)
+    # End to end through the host-buffer entry points, every step's copy of phi in and
+    # of labels, sizes, histogram and count out inside the timed region.  The headline
+    # form streams fields the way a simulation hands over snapshots: the asynchronous
+    # entry on --e2e-streams contexts, each on its own stream, taking steps in turn,
+    # so that one step's copy in overlaps another's copy out.  The synchronous entry
+    # (one step at a time) is reported beside it.
     e2e = None
     if not args.no_e2e:
+        k_e2e = max(3, min(args.steps, 20))
+        cap_h = 2 * n_clusters + 1024            # host sizes buffers: the count fits with room
         phi_h = torch.empty((L, L, L), dtype=torch.float32, pin_memory=True)
         phi_h.copy_(phi)
-        lab_h = torch.empty((L, L, L), dtype=torch.int32, pin_memory=True)
-        sizes_h = torch.empty(cap, dtype=torch.int64, pin_memory=True)
-        hist_h = torch.empty(32, dtype=torch.int64, pin_memory=True)
-        ncl_h = torch.empty(1, dtype=torch.int64, pin_memory=True)
-        ph = hk._stream_handle(stream)
+        nstr = max(1, args.e2e_streams)
+        outs_h = [(torch.empty((L, L, L), dtype=torch.int32, pin_memory=True),
+                   torch.empty(cap_h, dtype=torch.int64, pin_memory=True),
+                   torch.empty(32, dtype=torch.int64, pin_memory=True),
+                   torch.empty(1, dtype=torch.int64, pin_memory=True)) for _ in range(nstr)]
+        more = [hk.Labeller(local) for _ in range(nstr - 1)]
+        for m in more:
+            if args.tile:
+                m.set_tile(*[int(v) for v in args.tile.split(",")])
+        labs = [lab] + more
+        streams = [stream] + [torch.cuda.Stream() for _ in range(nstr - 1)]
 
-        def e2e_step():
-            rc = hk.hk_label_host(lab.ctx, phi_h.data_ptr(), L, L, L, per, lab_h.data_ptr(), sizes_h.data_ptr(),
-                                  cap, hist_h.data_ptr(), ncl_h.data_ptr(), ph)
+        def async_step(i):
+            j = i % nstr
+            labs[j].label_host_async(phi_h, *outs_h[j], per, stream=streams[j])
+
+        def sync_step():
+            o = outs_h[0]
+            rc = hk.hk_label_host(lab.ctx, phi_h.data_ptr(), L, L, L, per, o[0].data_ptr(), o[1].data_ptr(),
+                                  cap_h, o[2].data_ptr(), o[3].data_ptr(), hk._stream_handle(stream))
             assert rc == hk.HK_OK, rc
 
-        e2e_step()
-        k_e2e = max(3, min(args.steps, 10))
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(k_e2e):
-            e2e_step()
-        barrier()
-        ms_e2e = max_over_ranks((time.perf_counter() - t0) / k_e2e * 1e3, dist)
-        assert int(ncl_h[0]) == n_clusters
-        e2e = {"value": job_gsites_per_s(world, N, ms_e2e), "unit": "Gsites/s", "ms_per_step": ms_e2e,
-               "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 4 * N + 8 * n_clusters + 8 * 32 + 8,
-               "entry": "hk_label_host (pinned host buffers)"}
-        del phi_h, lab_h, sizes_h
+        def timed(run):
+            barrier()
+            t0 = time.perf_counter()
+            run()
+            for st in streams:
+                st.synchronize()
+            barrier()
+            return max_over_ranks((time.perf_counter() - t0) / k_e2e * 1e3, dist)
+
+        for i in range(nstr):
+            async_step(i)
+        torch.cuda.synchronize()
+        ms_async = timed(lambda: [async_step(i) for i in range(k_e2e)])
+        for o in outs_h:
+            assert int(o[3][0]) == n_clusters
+        assert torch.equal(outs_h[0][0], labels.cpu()) and torch.equal(outs_h[0][1][:n_clusters], sizes[:n_clusters].cpu())
+        sync_step()
+        ms_sync = timed(lambda: [sync_step() for _ in range(k_e2e)])
+        assert int(outs_h[0][3][0]) == n_clusters
+        d2h = 4 * N + 8 * n_clusters + 8 * 32 + 8
+        e2e = {"value": job_gsites_per_s(world, N, ms_async), "unit": "Gsites/s", "ms_per_step": ms_async,
+               "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": d2h,
+               "entry": f"hk_label_host_async (pinned host buffers), {nstr} contexts on {nstr} streams taking "
+                        "steps in turn: one step's copy in overlaps another's copy out",
+               "steps": k_e2e,
+               "sync": {"value": job_gsites_per_s(world, N, ms_sync), "ms_per_step": ms_sync,
+                        "entry": "hk_label_host, one step at a time"}}
+        for m in more:
+            m.close()
+        del phi_h, outs_h
 
     extra = None
     if rank == 0 and not args.no_extra:

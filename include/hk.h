@@ -164,6 +164,34 @@ int hk_label_host(hk_ctx *ctx, const float *phi_host, int nx, int ny, int nz, co
                   int32_t *labels_host, int64_t *sizes_host, int64_t sizes_cap,
                   int64_t *hist_host, int64_t *n_clusters_host, void *stream);
 
+/* hk_label_host without the wait, so that consecutive fields stream through
+ * the host link: a simulation hands over snapshot i+1 while the labels of
+ * snapshot i are still coming back.  Enqueues on `stream`, in order, the copy
+ * of phi host->device, the labelling, the copies of the count, the labels and
+ * the histogram back, and a kernel that writes the first min(count, sizes_cap)
+ * sizes straight into sizes_host; then returns.  The paper has no counterpart
+ * (its fields stay in the simulation's memory); this is a property of the
+ * library.
+ *
+ * Arguments as hk_label_host, except:
+ *   - every host buffer must be page-locked and device-accessible
+ *     (cudaHostAlloc, cudaMallocHost or cudaHostRegister): a pageable one is
+ *     rejected with HK_ERR_ARG before anything is enqueued;
+ *   - host buffers are read and written after the call returns: phi_host must
+ *     stay unchanged and the outputs unread until the stream has reached the
+ *     end of the call (cudaStreamSynchronize, or an event recorded after it);
+ *   - there is no capacity error: after completion, *n_clusters_host >
+ *     sizes_cap means sizes_host holds only the first sizes_cap sizes
+ *     (labels, histogram and count are complete either way);
+ *   - n_clusters_host may be NULL.
+ * Calls on one context are ordered by its stream rule (above): one context per
+ * stream.  Two contexts on two streams, used for alternate fields, overlap one
+ * field's phi copy with the other's label copy.
+ * Errors: HK_ERR_ARG, HK_ERR_TOO_LARGE, HK_ERR_NOMEM, HK_ERR_CUDA. */
+int hk_label_host_async(hk_ctx *ctx, const float *phi_host, int nx, int ny, int nz, const int periodic[3],
+                        int32_t *labels_host, int64_t *sizes_host, int64_t sizes_cap,
+                        int64_t *hist_host, int64_t *n_clusters_host, void *stream);
+
 /* hk_label without any device allocation, for callers that cannot allocate
  * device memory (for example a simulation that has handed all free device
  * memory to its own allocator, or a loop in which a cudaMalloc/cudaFree would

@@ -202,8 +202,9 @@ void fold_timing(hk_ctx *ctx, int slot) {
 // index_field (one lattice only): the lattice is an index field; label its far sites
 // (I < -0.5) and, when inside != nullptr, write the interior/exterior tags of its
 // clusters to inside.
+// check_capacity == false: never wait for the counts (the caller compares them).
 int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st, bool index_field = false,
-                 int8_t *inside = nullptr) {
+                 int8_t *inside = nullptr, bool check_capacity = true) {
     TileInfo ti;
     if (!hk::tile_info(ctx->ty, ctx->tz, ti)) return HK_ERR_ARG;
     for (int i = 0; i < n; ++i) {
@@ -307,7 +308,7 @@ int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st, bo
             const hk_lattice &l = lats[c0 + i];
             const int64_t N = (int64_t)l.nx * l.ny * l.nz;
             if (!dev[i].ncl) dev[i].ncl = slots + i;
-            if (dev[i].sizes_cap < (N + 1) / 2) chunk_check = true;
+            if (check_capacity && dev[i].sizes_cap < (N + 1) / 2) chunk_check = true;
         }
         cudaEvent_t *ev = nullptr;
         if (ctx->timing) {
@@ -338,6 +339,44 @@ int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st, bo
     if (any_check)
         for (int i = 0; i < n; ++i)
             if (counts[i] > lats[i].sizes_cap) return HK_ERR_CAPACITY;
+    return HK_OK;
+}
+
+// Device copies of hk_label_host / hk_label_host_async in the context's io buffer
+// (grown on demand): phi, labels, histogram, count and sizes.
+struct HostIo {
+    float *phi;
+    int32_t *labels;
+    int64_t *hist, *ncl, *sizes;
+    hk_lattice lattice(int nx, int ny, int nz, const int periodic[3], int64_t sizes_cap) const {
+        hk_lattice l;
+        l.phi = phi;
+        l.nx = nx; l.ny = ny; l.nz = nz;
+        for (int a = 0; a < 3; ++a) l.periodic[a] = periodic[a];
+        l.labels = labels;
+        l.sizes = sizes;
+        l.sizes_cap = sizes_cap;
+        l.hist = hist;
+        l.n_clusters = ncl;
+        return l;
+    }
+};
+
+int host_io(hk_ctx *ctx, int64_t N, int64_t sizes_cap, HostIo &io) {
+    const size_t o_phi = 0, o_lab = align256(4 * N), o_hist = o_lab + align256(4 * N);
+    const size_t o_ncl = o_hist + 256, o_sizes = o_ncl + 256;
+    const size_t need = o_sizes + align256(8 * (size_t)std::max<int64_t>(sizes_cap, 1));
+    if (need > ctx->io_bytes) {
+        if (ctx->io) { cudaDeviceSynchronize(); cudaFree(ctx->io); ctx->io = nullptr; ctx->io_bytes = 0; }
+        if (cudaMalloc(&ctx->io, need) != cudaSuccess) { cudaGetLastError(); return HK_ERR_NOMEM; }
+        ctx->io_bytes = need;
+    }
+    char *b = static_cast<char *>(ctx->io);
+    io.phi = reinterpret_cast<float *>(b + o_phi);
+    io.labels = reinterpret_cast<int32_t *>(b + o_lab);
+    io.hist = reinterpret_cast<int64_t *>(b + o_hist);
+    io.ncl = reinterpret_cast<int64_t *>(b + o_ncl);
+    io.sizes = reinterpret_cast<int64_t *>(b + o_sizes);
     return HK_OK;
 }
 
@@ -493,47 +532,68 @@ int hk_label_host(hk_ctx *ctx, const float *phi_host, int nx, int ny, int nz, co
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return fail_cuda(ctx, e);
-    const size_t o_phi = 0, o_lab = align256(4 * N), o_hist = o_lab + align256(4 * N);
-    const size_t o_ncl = o_hist + 256, o_sizes = o_ncl + 256;
-    const size_t need = o_sizes + align256(8 * (size_t)std::max<int64_t>(sizes_cap, 1));
-    if (need > ctx->io_bytes) {
-        if (ctx->io) { cudaDeviceSynchronize(); cudaFree(ctx->io); ctx->io = nullptr; ctx->io_bytes = 0; }
-        if (cudaMalloc(&ctx->io, need) != cudaSuccess) { cudaGetLastError(); return HK_ERR_NOMEM; }
-        ctx->io_bytes = need;
-    }
-    char *io = static_cast<char *>(ctx->io);
-    float *phi_d = reinterpret_cast<float *>(io + o_phi);
-    int32_t *lab_d = reinterpret_cast<int32_t *>(io + o_lab);
-    int64_t *hist_d = reinterpret_cast<int64_t *>(io + o_hist);
-    int64_t *ncl_d = reinterpret_cast<int64_t *>(io + o_ncl);
-    int64_t *sizes_d = reinterpret_cast<int64_t *>(io + o_sizes);
-    e = cudaMemcpyAsync(phi_d, phi_host, 4 * N, cudaMemcpyHostToDevice, st);
+    HostIo io;
+    int rc = host_io(ctx, N, sizes_cap, io);
+    if (rc != HK_OK) return rc;
+    e = cudaMemcpyAsync(io.phi, phi_host, 4 * N, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return fail_cuda(ctx, e);
-    hk_lattice l;
-    l.phi = phi_d;
-    l.nx = nx; l.ny = ny; l.nz = nz;
-    for (int a = 0; a < 3; ++a) l.periodic[a] = periodic[a];
-    l.labels = lab_d;
-    l.sizes = sizes_d;
-    l.sizes_cap = sizes_cap;
-    l.hist = hist_d;
-    l.n_clusters = ncl_d;
-    int rc = run_lattices(ctx, &l, 1, st);
+    hk_lattice l = io.lattice(nx, ny, nz, periodic, sizes_cap);
+    rc = run_lattices(ctx, &l, 1, st);
     if (rc != HK_OK && rc != HK_ERR_CAPACITY) return rc;
     int64_t ncl = 0;
-    e = cudaMemcpyAsync(&ncl, ncl_d, 8, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(labels_host, lab_d, 4 * N, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && hist_host) e = cudaMemcpyAsync(hist_host, hist_d, 256, cudaMemcpyDeviceToHost, st);
+    e = cudaMemcpyAsync(&ncl, io.ncl, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(labels_host, io.labels, 4 * N, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && hist_host) e = cudaMemcpyAsync(hist_host, io.hist, 256, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail_cuda(ctx, e);
     const int64_t ns = std::min(ncl, sizes_cap);
     if (ns > 0) {
-        e = cudaMemcpyAsync(sizes_host, sizes_d, 8 * ns, cudaMemcpyDeviceToHost, st);
+        e = cudaMemcpyAsync(sizes_host, io.sizes, 8 * ns, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return fail_cuda(ctx, e);
     }
     if (n_clusters_host) *n_clusters_host = ncl;
     return ncl > sizes_cap ? HK_ERR_CAPACITY : HK_OK;
+}
+
+int hk_label_host_async(hk_ctx *ctx, const float *phi_host, int nx, int ny, int nz, const int periodic[3],
+                        int32_t *labels_host, int64_t *sizes_host, int64_t sizes_cap, int64_t *hist_host,
+                        int64_t *n_clusters_host, void *stream) {
+    if (!ctx || !periodic || !phi_host || !labels_host) return HK_ERR_ARG;
+    if (nx < 1 || ny < 1 || nz < 1 || sizes_cap < 0 || (sizes_cap > 0 && !sizes_host)) return HK_ERR_ARG;
+    const int64_t N = (int64_t)nx * ny * nz;
+    if (N >= MAX_SITES) return HK_ERR_TOO_LARGE;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return fail_cuda(ctx, e);
+    // every host buffer page-locked; the sizes are written by a kernel, through the
+    // buffer's device address
+    int64_t *sizes_dst = nullptr;
+    {
+        const void *bufs[5] = {phi_host, labels_host, sizes_cap > 0 ? sizes_host : nullptr, hist_host,
+                               n_clusters_host};
+        for (int i = 0; i < 5; ++i) {
+            if (!bufs[i]) continue;
+            cudaPointerAttributes a;
+            if (cudaPointerGetAttributes(&a, bufs[i]) != cudaSuccess) { cudaGetLastError(); return HK_ERR_ARG; }
+            if (a.type != cudaMemoryTypeHost || !a.devicePointer) return HK_ERR_ARG;
+            if (i == 2) sizes_dst = static_cast<int64_t *>(a.devicePointer);
+        }
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    HostIo io;
+    int rc = host_io(ctx, N, sizes_cap, io);
+    if (rc != HK_OK) return rc;
+    e = cudaMemcpyAsync(io.phi, phi_host, 4 * N, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return fail_cuda(ctx, e);
+    hk_lattice l = io.lattice(nx, ny, nz, periodic, sizes_cap);
+    rc = run_lattices(ctx, &l, 1, st, false, nullptr, false);
+    if (rc != HK_OK) return rc;
+    if (n_clusters_host) e = cudaMemcpyAsync(n_clusters_host, io.ncl, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(labels_host, io.labels, 4 * N, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && hist_host) e = cudaMemcpyAsync(hist_host, io.hist, 256, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && sizes_dst) e = hk::launch_copy_counted(io.sizes, io.ncl, sizes_cap, sizes_dst, st);
+    if (e != cudaSuccess) return fail_cuda(ctx, e);
+    return HK_OK;
 }
 
 int hk_set_tile(hk_ctx *ctx, int ty, int tz) {

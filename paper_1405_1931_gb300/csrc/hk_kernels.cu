@@ -1056,6 +1056,28 @@ cudaError_t launch_interior(const LatDev &L, const Work &W, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Copy sized on the device: the host does not know the cluster count when it enqueues
+// the copy of the sizes, so a grid-stride kernel reads it and copies that many (dst
+// may be page-locked host memory, written across the host link).
+__global__ void __launch_bounds__(256) k_copy_counted(const int64_t *src, const int64_t *count, int64_t cap,
+                                                       int64_t *dst) {
+    const int64_t n = min(*count, cap);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = __ldcs(src + i);
+}
+
+cudaError_t launch_copy_counted(const int64_t *src, const int64_t *count, int64_t cap, int64_t *dst,
+                                cudaStream_t st) {
+    if (cap <= 0) return cudaSuccess;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int64_t g = (cap + 255) / 256;
+    if (g > (int64_t)nsm * 8) g = (int64_t)nsm * 8;
+    k_copy_counted<<<(unsigned)(g > 0 ? g : 1), 256, 0, st>>>(src, count, cap, dst);
+    return cudaGetLastError();
+}
+
 // --------------------------------------------------------------------------------------
 // launch sequence
 // --------------------------------------------------------------------------------------

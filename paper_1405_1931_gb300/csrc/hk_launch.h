@@ -43,5 +43,9 @@ cudaError_t launch_label(int ty, int tz, const LatDev *lats, int n, const Plan &
 // Interior/exterior tags of a lattice labelled with occ_mode 1 (after launch_label on
 // the same stream; needs W.rootbits and W.votes).
 cudaError_t launch_interior(const LatDev &L, const Work &W, cudaStream_t st);
+// dst[i] = src[i] for i < min(*count, cap): a copy sized on the device (dst may be
+// device-accessible host memory)
+cudaError_t launch_copy_counted(const int64_t *src, const int64_t *count, int64_t cap, int64_t *dst,
+                                cudaStream_t st);
 
 }  // namespace hk

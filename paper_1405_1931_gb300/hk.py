@@ -20,7 +20,7 @@ HK_OK, HK_ERR_ARG, HK_ERR_TOO_LARGE, HK_ERR_CAPACITY = 0, 1, 2, 3
 HK_ERR_CUDA, HK_ERR_TIMEOUT, HK_ERR_NOMEM = 4, 5, 6
 
 EXPORTED = ("hk_create", "hk_destroy", "hk_workspace_bytes", "hk_reserve", "hk_label", "hk_label_batched",
-            "hk_label_host", "hk_set_tile", "hk_set_timing", "hk_get_timing", "hk_sync_status", "hk_set_graphs", "hk_last_cuda_error", "hk_strerror", "hk_label_noalloc",
+            "hk_label_host", "hk_label_host_async", "hk_set_tile", "hk_set_timing", "hk_get_timing", "hk_sync_status", "hk_set_graphs", "hk_last_cuda_error", "hk_strerror", "hk_label_noalloc",
             "hk_label_interior", "hk_rc_histogram",
             "hk_gen_iid", "hk_gen_spheres", "hk_gen_spheres_dev", "hk_gen_capsule")
 
@@ -62,6 +62,7 @@ def load():
             "hk_label": (I, [P, P, I, I, I, P, P, P, I64, P, P, P]),
             "hk_label_batched": (I, [P, ctypes.POINTER(hk_lattice), I, P]),
             "hk_label_host": (I, [P, P, I, I, I, P, P, P, I64, P, P, P]),
+            "hk_label_host_async": (I, [P, P, I, I, I, P, P, P, I64, P, P, P]),
             "hk_label_noalloc": (I, [P, I, I, I, P, P, P, I64, P, P, P]),
             "hk_label_interior": (I, [P, P, I, I, I, P, P, P, I64, P, P, P, P]),
             "hk_rc_histogram": (I, [P, P, I64, P, I, P, P, I, P]),
@@ -153,6 +154,12 @@ def hk_label_host(ctx, phi_host, nx, ny, nz, periodic, labels_host, sizes_host, 
                   n_clusters_host, stream=0) -> int:
     return load().hk_label_host(ctx, phi_host, nx, ny, nz, _per(periodic), labels_host, sizes_host,
                                 int(sizes_cap), hist_host, n_clusters_host, stream)
+
+
+def hk_label_host_async(ctx, phi_host, nx, ny, nz, periodic, labels_host, sizes_host, sizes_cap, hist_host,
+                        n_clusters_host, stream=0) -> int:
+    return load().hk_label_host_async(ctx, phi_host, nx, ny, nz, _per(periodic), labels_host, sizes_host,
+                                      int(sizes_cap), hist_host, n_clusters_host, stream)
 
 
 def hk_label_noalloc(phi, nx, ny, nz, periodic, labels_out, sizes_out, sizes_cap, hist_out, n_clusters_out,
@@ -345,3 +352,14 @@ class Labeller:
             raise HKError(rc, "hk_label_host")
         k = int(ncl[0])
         return labels, sizes[:min(k, cap)], hist, k
+
+    def label_host_async(self, phi, labels, sizes, hist, ncl, periodic=(1, 1, 1), stream=None):
+        """Enqueue one field held in page-locked host tensors (torch, pin_memory=True)
+        and return; the outputs are valid once `stream` has passed the call, when
+        sizes holds the first min(ncl[0], len(sizes)) sizes."""
+        nz, ny, nx = phi.shape
+        rc = hk_label_host_async(self.ctx, phi.data_ptr(), nx, ny, nz, periodic, labels.data_ptr(),
+                                 sizes.data_ptr(), sizes.numel(), hist.data_ptr(), ncl.data_ptr(),
+                                 _stream_handle(stream))
+        if rc != HK_OK:
+            raise HKError(rc, "hk_label_host_async")
