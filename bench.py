@@ -225,7 +225,8 @@ def time_single(lab, phi, per, reps, flush=None):
 
 
 def extra_configs(args, peak):
-    """The other workloads: 32^3, 256^3 emulsion, capsule interiors, the uneven batch, the served stream."""
+    """The other workloads: 32^3, 256^3 emulsion, the block benchmark sweep at 1024^3, capsule
+    interiors, the uneven batch, the served stream."""
     import torch
     from paper_1405_1931_gb300 import autotune, fields, hk, serve
     res = {}
@@ -250,6 +251,22 @@ def extra_configs(args, peak):
     ms, ncl = time_single(lab, phi, (1, 1, 1), 20, flush)
     line("emulsion256", L ** 3, ms, ncl, "256^3 emulsion, 600 droplets r in [5,15], periodic", "L2 flushed between reps")
     del phi
+
+    # The benchmark of Sec. 3: 1024^3 filled with alternating cubic domains of b^3 sites
+    # that touch only at edges and corners, so n_clusters = (1024 / b)^3 / 2 runs from 32
+    # (b = 256) to the maximum V / 2 (b = 1, the site checkerboard).
+    L = 1024
+    sweep = []
+    for b in (256, 128, 64, 32, 16, 8, 4, 2, 1):
+        phi = fields.block_field_device(L, b)
+        ms, ncl = time_single(lab, phi, (1, 1, 1), 5)
+        assert ncl == (L // b) ** 3 // 2, (b, ncl)
+        sweep.append({"b": b, "n_clusters": ncl, "ms": ms, "gsites_per_s": L ** 3 / (ms * 1e-3) / 1e9})
+        del phi
+        torch.cuda.empty_cache()
+    res["block_sweep1024"] = {"workload": "Sec. 3 benchmark pattern at 1024^3: alternating cubic domains of b^3 "
+                                          "sites, periodic; n_clusters from 32 to V/2",
+                              "points": sweep, "cache": "inputs larger than L2"}
 
     # interior/exterior of closed membranes (Sec. 6, steps 3-5): 256^3 index field, 24 capsules
     shape = (256, 256, 256)

@@ -827,7 +827,6 @@ struct FlatSmem {
     using SH = TileShape<TY, TZ>;
     alignas(1024) int32_t stage[SH::SITES];   // labels [lz][ly][x], swizzled (TMA store source)
     static constexpr int GL = SH::MAX_BOUNDARY < 384 ? SH::MAX_BOUNDARY : 384;   // staged boundary pieces
-    uint16_t code[SH::MAXRUNS];
     int gl[GL];                               // label of each boundary piece's cluster
     int gsize[GL];                            // cluster size if the piece is the cluster root, else -1
     int warp_tmp[32];
@@ -859,7 +858,7 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapBa
         const TileGeo g = tile_geo<TY, TZ>(L, t);
         const bool use_tma = TB.tm[lat].valid && stage_ok;
         const int4 ti = W.tinfo[t];
-        const int base = ti.x, nb = ti.y, total = ti.z;
+        const int base = ti.x, nb = ti.y;
         const int r = tid, ly = r % TY, lz = r / TY;
         const uint32_t m = W.mask[t * R + r];
         const uint32_t rs = run_starts(m);
@@ -885,7 +884,6 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapBa
         }
 
         const uint16_t *C = W.codes + t * MR;
-        for (int i = tid; i < total; i += NT) S.code[i] = C[i];
         for (int k = tid; k < nb && k < FlatSmem<TY, TZ>::GL; k += NT) {
             S.gl[k] = __ldg(W.key + base + k);       // cluster label (written by piece_finalize)
             S.gsize[k] = __ldg(W.psize + base + k);  // cluster size at the root piece, else -1
@@ -906,7 +904,7 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapBa
         while (w) {
             const int x0 = __ffs(w) - 1;
             w &= w - 1;
-            const int c = S.code[id++];
+            const int c = __ldg(C + id++);   // a row's codes are consecutive: L1 lines serve them
             const int k = c & CODE_LOW;
             const bool isb = (c & CODE_BOUNDARY) != 0, isr = (c & CODE_ROOT) != 0;
             const int kk = k < FlatSmem<TY, TZ>::GL ? k : 0;

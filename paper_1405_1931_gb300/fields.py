@@ -69,6 +69,29 @@ def constant_field(nx: int, ny: int, nz: int, value: float) -> np.ndarray:
     return np.full((nz, ny, nx), value, dtype=np.float32)
 
 
+def block_field_device(L: int, b: int, device="cuda"):
+    """The benchmark pattern of Sec. 3 on an L^3 lattice, built on the device with torch:
+    cubic domains of b^3 sites, domain (i, j, k) occupied (phi = +1) iff i + j + k is
+    even, else phi = -1.  Occupied domains touch only along edges and corners, so with
+    an even number L / b of domains per axis (also across periodic wraps) there are
+    (L / b)^3 / 2 clusters of b^3 sites; b = 1 is the site checkerboard, V / 2 clusters."""
+    import torch
+    c = (torch.div(torch.arange(L, device=device, dtype=torch.int32), b, rounding_mode="floor") & 1).to(torch.int8)
+    par = (c.view(L, 1, 1) + c.view(1, L, 1) + c.view(1, 1, L)) & 1
+    return (1 - 2 * par).to(torch.float32)
+
+
+def block_labels_device(L: int, b: int, device="cuda"):
+    """Closed-form labels of block_field_device(L, b): the smallest row-major index of
+    each occupied domain (its corner), -1 for the medium."""
+    import torch
+    c = torch.div(torch.arange(L, device=device, dtype=torch.int32), b, rounding_mode="floor")
+    corner = c * b
+    lab = (corner.view(L, 1, 1) * (L * L) + corner.view(1, L, 1) * L + corner.view(1, 1, L))
+    par = (c.view(L, 1, 1) + c.view(1, L, 1) + c.view(1, 1, L)) & 1
+    return torch.where(par == 0, lab, torch.full_like(lab, -1))
+
+
 def sphere_params(n_spheres: int, box: tuple, seed: int, r_lo: float = 5.0, r_hi: float = 15.0):
     """Centres uniform in the box and radii uniform in [r_lo, r_hi] from stream ``seed``.
 

@@ -4,7 +4,10 @@ bench.py times (default tile 32x16x16, device-resident fields).
 - 1024^3 critical site percolation (p = 0.3116, periodic xyz): every label, size and
   histogram bin against the oracle (about 10 s of serial CPU work);
 - the full 96-lattice uneven batch (axes up to 384), labelled in one batched call,
-  every lattice against the oracle.
+  every lattice against the oracle;
+- the benchmark pattern of Sec. 3 at 1024^3 (alternating cubic domains touching only at
+  edges and corners), against its closed form: (1024 / b)^3 / 2 clusters of b^3 sites,
+  each labelled by its corner; b = 1 is the maximum V / 2 clusters.
 The fields are generated on the device and copied to the host, so the oracle labels
 exactly the bytes the GPU labels.
 """
@@ -67,3 +70,19 @@ def test_uneven_batch_96_full_parity(labeller):
         assert np.array_equal(labels.cpu().numpy(), want[0]), prm
         assert np.array_equal(sizes[:n].cpu().numpy(), want[1]), prm
         assert np.array_equal(hist.cpu().numpy(), want[2]), prm
+
+
+@pytest.mark.parametrize("b", [1, 2, 16, 256])
+def test_block_benchmark_1024_closed_form(labeller, b):
+    L = 1024
+    phi = fields.block_field_device(L, b)
+    labels, sizes, hist, ncl = labeller.label(phi, (1, 1, 1))
+    labeller.sync_status()
+    del phi
+    n = int(ncl.item())
+    assert n == (L // b) ** 3 // 2
+    assert bool((sizes[:n] == b ** 3).all())
+    want_hist = torch.zeros(32, dtype=torch.int64, device="cuda")
+    want_hist[(b ** 3).bit_length() - 1] = n
+    assert torch.equal(hist, want_hist)
+    assert torch.equal(labels, fields.block_labels_device(L, b))

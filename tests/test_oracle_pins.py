@@ -171,6 +171,19 @@ def test_block_benchmark_pattern(case):
         assert hist[case["expected_size"][0].bit_length() - 1] == n
 
 
+@pytest.mark.parametrize("L,b", [(8, 1), (16, 2), (16, 4), (32, 8)])
+def test_block_benchmark_closed_form_helpers(L, b):
+    """The closed form used at 1024^3 on the GPU (fields.block_field_device / block_labels_device,
+    run here with torch on the CPU) agrees with the oracle: corner labels, (L/b)^3/2 clusters of b^3."""
+    torch = pytest.importorskip("torch")
+    from paper_1405_1931_gb300 import fields
+    phi = fields.block_field_device(L, b, device="cpu").numpy()
+    labels, sizes, hist, n = oracle.label(phi, (1, 1, 1))
+    np.testing.assert_array_equal(labels, fields.block_labels_device(L, b, device="cpu").numpy())
+    assert n == (L // b) ** 3 // 2 and (sizes == b ** 3).all()
+    assert hist[(b ** 3).bit_length() - 1] == n
+
+
 def test_checkerboard_odd_periodic_axis():
     """Odd periodic axis: the wrap joins (nx-1, y, z) and (0, y, z), which have the same parity.
 
