@@ -5,6 +5,9 @@ bench.py times (default tile 32x16x16, device-resident fields).
   histogram bin against the oracle (about 10 s of serial CPU work);
 - the full 96-lattice uneven batch (axes up to 384), labelled in one batched call,
   every lattice against the oracle;
+- the largest lattice the library takes: 1291 x 1290 x 1289 = 2,146,687,710 sites, just below
+  2^31, ragged along every axis, critical percolation, periodic xyz, against the oracle
+  (site indices, labels and keys near the int32 limit);
 - the benchmark pattern of Sec. 3 at 1024^3 (alternating cubic domains touching only at
   edges and corners), against its closed form: (1024 / b)^3 / 2 clusters of b^3 sites,
   each labelled by its corner; b = 1 is the maximum V / 2 clusters.
@@ -86,3 +89,27 @@ def test_block_benchmark_1024_closed_form(labeller, b):
     want_hist[(b ** 3).bit_length() - 1] = n
     assert torch.equal(hist, want_hist)
     assert torch.equal(labels, fields.block_labels_device(L, b))
+
+
+def test_near_max_sites_full_parity(labeller):
+    from paper_1405_1931_gb300 import hk
+    nx, ny, nz = 1291, 1290, 1289
+    assert nx * ny * nz < 2 ** 31 and nx * ny * nz > 2 ** 31 - 2 ** 20
+    phi = torch.empty((nz, ny, nx), dtype=torch.float32, device="cuda")
+    assert hk.hk_gen_iid(phi.data_ptr(), nx, ny, nz, 7, fields.P_C_SIMPLE_CUBIC, 0) == 0
+    labels, sizes, hist, ncl = labeller.label(phi, (1, 1, 1))
+    labeller.sync_status()
+    n = int(ncl.item())
+    phi_h = phi.cpu().numpy()
+    del phi
+    got_labels = labels.cpu().numpy()
+    got_sizes = sizes[:n].cpu().numpy()
+    got_hist = hist.cpu().numpy()
+    del labels, sizes, hist
+    torch.cuda.empty_cache()
+    want = oracle.label(phi_h, (1, 1, 1))
+    del phi_h
+    assert n == want[3]
+    assert np.array_equal(got_sizes, want[1])
+    assert np.array_equal(got_hist, want[2])
+    assert np.array_equal(got_labels, want[0])
