@@ -65,6 +65,12 @@ def _bind(lib):
     g.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                   ctypes.c_void_p]
+    st = lib.hk_oracle_interior_state
+    st.restype = ctypes.c_int
+    st.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    up = lib.hk_oracle_interior_update
+    up.restype = ctypes.c_int
+    up.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
     return lib
 
 
@@ -121,6 +127,41 @@ def interior(index: np.ndarray, periodic=(1, 1, 1), sizes_cap: int | None = None
         raise RuntimeError(f"hk_oracle_interior failed with status {rc}")
     k = min(int(ncl[0]), int(sizes_cap))
     return labels, sizes[:k].copy(), hist, int(ncl[0]), inside[:k].copy()
+
+
+def interior_state(index: np.ndarray, periodic=(1, 1, 1), lib=None) -> np.ndarray:
+    """Interior state of every site (Sec. 6): int8, 1 inside, 0 outside, -1 undetermined.
+
+    Far sites (I < -0.5) take their cluster's tag (``interior``); near sites the
+    side their value names (I < 0: 1, else 0).
+    """
+    lib = lib or load()
+    index = np.ascontiguousarray(index, dtype=np.float32)
+    if index.ndim != 3:
+        raise ValueError("index must have shape (nz, ny, nx)")
+    nz, ny, nx = index.shape
+    state = np.empty(index.shape, dtype=np.int8)
+    per = np.array([int(bool(p)) for p in periodic], dtype=np.int32)
+    rc = lib.hk_oracle_interior_state(index.ctypes.data, nx, ny, nz, per.ctypes.data, state.ctypes.data)
+    if rc != OK:
+        raise RuntimeError(f"hk_oracle_interior_state failed with status {rc}")
+    return state
+
+
+def interior_update(state_prev: np.ndarray, index: np.ndarray, lib=None) -> np.ndarray:
+    """Incremental interior state for slowly moving membranes (Sec. 6, last paragraph):
+    sites near a membrane now (I >= -0.5) take the side their value names (I < 0: 1,
+    else 0); every other site keeps its previous state."""
+    lib = lib or load()
+    state_prev = np.ascontiguousarray(state_prev, dtype=np.int8)
+    index = np.ascontiguousarray(index, dtype=np.float32)
+    if state_prev.shape != index.shape:
+        raise ValueError("state_prev and index must have one shape")
+    out = np.empty(index.shape, dtype=np.int8)
+    rc = lib.hk_oracle_interior_update(state_prev.ctypes.data, index.ctypes.data, int(index.size), out.ctypes.data)
+    if rc != OK:
+        raise RuntimeError(f"hk_oracle_interior_update failed with status {rc}")
+    return out
 
 
 def rc_histogram(sizes, edges, lib=None):

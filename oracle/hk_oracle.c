@@ -64,6 +64,22 @@
  *     undetermined (-1).  inside_out[k] is the tag of the cluster with
  *     compacted id k+1.
  *
+ * hk_oracle_interior_state gives every site its interior state (Sec. 6: 0 far
+ * outside, 1 far inside): a far site (I < -0.5) takes its cluster's tag from
+ * hk_oracle_interior (1 interior, 0 exterior, -1 undetermined); a near site
+ * takes the side its proximity value names (step 2: -d inside, +d outside),
+ * 1 for I < 0 and 0 otherwise.
+ *
+ * hk_oracle_interior_update is the cheaper step of the last paragraph of Sec. 6
+ * for membranes that move much less than a lattice constant per step: only the
+ * sites near a membrane now are updated, to the side their value names now;
+ * every other site keeps its previous state.  The paper's premise is that a
+ * membrane moves much less than a lattice constant per step, so a site that is
+ * far from every membrane now has not changed sides since the last step.  Under
+ * that premise the result equals hk_oracle_interior_state of the current field;
+ * a test checks this on capsules moving by under half a lattice constant per
+ * step, and shows that it fails for a jump of several lattice constants.
+ *
  * hk_oracle_rc_histogram bins cluster sizes V by R_c, the radius of a sphere of
  * volume V (Fig. 5 caption: (4 pi / 3) R_c^3 = V), with caller-given ascending
  * edges e_0 < ... < e_{m-1}.  R_c >= e is decided as V >= t(e) with
@@ -92,6 +108,9 @@ int hk_oracle_interior(const float *index, int nx, int ny, int nz, const int per
                        int64_t *hist_out, int64_t *n_clusters_out, int8_t *inside_out);
 int hk_oracle_rc_histogram(const int64_t *sizes, int64_t n, const double *edges, int n_edges,
                            int64_t *hist_out, double *rc_sum_out);
+int hk_oracle_interior_state(const float *index, int nx, int ny, int nz, const int periodic[3],
+                             int8_t *state_out);
+int hk_oracle_interior_update(const int8_t *state_prev, const float *index, int64_t n, int8_t *state_out);
 
 int hk_oracle_version(void) { return 1; }
 
@@ -316,5 +335,41 @@ int hk_oracle_rc_histogram(const int64_t *sizes, int64_t n, const double *edges,
         rc_sum += cbrt(V / four_thirds_pi);
     }
     if (rc_sum_out) *rc_sum_out = rc_sum;
+    return HKO_OK;
+}
+
+/* Side of a near site named by its proximity value (Sec. 6, step 2). */
+static int8_t near_side(float v) { return (int8_t)(v < 0.0f ? 1 : 0); }
+
+int hk_oracle_interior_state(const float *index, int nx, int ny, int nz, const int periodic[3],
+                             int8_t *state_out) {
+    if (!index || !periodic || !state_out) return HKO_ERR_ARG;
+    if (nx < 1 || ny < 1 || nz < 1) return HKO_ERR_ARG;
+    const int64_t N = (int64_t)nx * ny * nz;
+    if (N >= ((int64_t)1 << 31)) return HKO_ERR_TOO_LARGE;
+    const int64_t cap = (N + 1) / 2;                 /* always enough clusters */
+    int32_t *labels = (int32_t *)malloc((size_t)N * sizeof(int32_t));
+    int64_t *sizes = (int64_t *)malloc((size_t)cap * sizeof(int64_t));
+    int8_t *inside = (int8_t *)malloc((size_t)cap);
+    int32_t *rank = (int32_t *)malloc((size_t)N * sizeof(int32_t));
+    int64_t hist[32], n = 0;
+    int rc = HKO_ERR_NOMEM;
+    if (labels && sizes && inside && rank) {
+        rc = hk_oracle_interior(index, nx, ny, nz, periodic, labels, sizes, cap, hist, &n, inside);
+        if (rc == HKO_OK) {
+            int32_t next = 0;
+            for (int64_t s = 0; s < N; ++s) if (labels[s] == s) rank[s] = next++;
+            for (int64_t s = 0; s < N; ++s)
+                state_out[s] = (index[s] < -0.5f) ? inside[rank[labels[s]]] : near_side(index[s]);
+        }
+    }
+    free(labels); free(sizes); free(inside); free(rank);
+    return rc;
+}
+
+int hk_oracle_interior_update(const int8_t *state_prev, const float *index, int64_t n, int8_t *state_out) {
+    if (n < 0 || (n > 0 && (!state_prev || !index || !state_out))) return HKO_ERR_ARG;
+    for (int64_t s = 0; s < n; ++s)
+        state_out[s] = (index[s] < -0.5f) ? state_prev[s] : near_side(index[s]);
     return HKO_OK;
 }

@@ -161,3 +161,20 @@ def interior_tags(index: np.ndarray, periodic):
                         votes[order[int(labels[az, ay, ax])]] += sign
     tags = np.array([1 if v < 0 else (0 if v > 0 else -1) for v in votes], dtype=np.int8)
     return labels, sizes, hist, n, tags
+
+
+def interior_state(index: np.ndarray, periodic):
+    """Per-site interior state from the definitions: a far site (I < -0.5) takes the
+    tag of its BFS cluster (interior_tags), a near site the side its value names:
+    1 for I < 0, else 0 (NaN: 0)."""
+    labels, _, _, _, tags = interior_tags(index, periodic)
+    roots = sorted({int(v) for v in labels.reshape(-1) if v >= 0})
+    order = {r: k for k, r in enumerate(roots)}
+    state = np.empty(index.shape, dtype=np.int8)
+    for pos in np.ndindex(index.shape):
+        v = float(index[pos])
+        if v < -0.5:
+            state[pos] = tags[order[int(labels[pos])]]
+        else:
+            state[pos] = 1 if v < 0 else 0
+    return state

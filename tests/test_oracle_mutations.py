@@ -8,12 +8,14 @@ the unmodified source.
 """
 import itertools
 import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
 
 import oracle
-from brute import bfs_label, interior_tags, log2_hist
+from brute import bfs_label, interior_state, interior_tags, log2_hist
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "hk_oracle.c")
 
@@ -44,6 +46,14 @@ MUTATIONS = {
     "interior_tag_swapped": ("(int8_t)(votes[k] < 0 ? 1 : votes[k] > 0 ? 0 : -1)",
                              "(int8_t)(votes[k] < 0 ? 1 : votes[k] > 0 ? 0 : 1)"),
     "interior_vote_x_only": ("for (int axis = 0; axis < 3; ++axis)", "for (int axis = 0; axis < 1; ++axis)"),
+    # per-site interior state and its incremental update (Sec. 6)
+    "state_near_side_le": ("return (int8_t)(v < 0.0f ? 1 : 0);", "return (int8_t)(v <= 0.0f ? 1 : 0);"),
+    "state_far_takes_side": ("(index[s] < -0.5f) ? inside[rank[labels[s]]] : near_side(index[s]);",
+                             "(index[s] < -0.5f) ? near_side(index[s]) : near_side(index[s]);"),
+    "update_keeps_near_sites": ("state_out[s] = (index[s] < -0.5f) ? state_prev[s] : near_side(index[s]);",
+                                "state_out[s] = state_prev[s];"),
+    "update_far_le": ("state_out[s] = (index[s] < -0.5f) ? state_prev[s] : near_side(index[s]);",
+                      "state_out[s] = (index[s] <= -0.5f) ? state_prev[s] : near_side(index[s]);"),
     # droplet-size histogram by R_c (Fig. 5)
     "rc_bin_shift": ("if (V >= ((e * e) * e) * four_thirds_pi) bin = b + 1;", "if (V >= ((e * e) * e) * four_thirds_pi) bin = b;"),
     "rc_radius_not_cubed": ("if (V >= ((e * e) * e) * four_thirds_pi) bin = b + 1;",
@@ -97,6 +107,15 @@ def battery(lib):
         want = interior_tags(I, per)
         same(got[:4], want[:4])
         np.testing.assert_array_equal(got[4], want[4])
+    # per-site interior state against the brute-force one, and the update rule by hand
+    for it in range(30):
+        shape = tuple(int(v) for v in rng.integers(1, 6, size=3))
+        I = values[rng.choice(len(values), size=shape, p=[0.5, 0.05, 0.2, 0.05, 0.15, 0.05])]
+        per = pers[it % 8]
+        np.testing.assert_array_equal(oracle.interior_state(I, per, lib=lib), interior_state(I, per))
+    st = np.array([1, 0, -1, 1, 0, 1, 0, 0], dtype=np.int8).reshape(1, 1, 8)
+    ix = np.array([-1.0, -1.0, -1.0, 0.25, -0.25, 0.0, np.nan, -0.5], dtype=np.float32).reshape(1, 1, 8)
+    assert oracle.interior_update(st, ix, lib=lib).reshape(-1).tolist() == [1, 0, -1, 0, 1, 0, 0, 1]
     # droplet-size histogram by R_c: hand-worked example
     h, rc_sum = oracle.rc_histogram([1, 8, 27, 1000], [0.5, 1.0, 2.0, 5.0, 10.0], lib=lib)
     assert h.tolist() == [0, 1, 2, 0, 1, 0]
@@ -113,15 +132,27 @@ def _build(tmp_path, name, mutation):
     src.write_text(text)
     out = tmp_path / f"lib{name}.so"
     oracle.build(str(src), str(out), extra=("-w",))
-    return oracle.load(str(out))
+    return str(out)
+
+
+def _battery_in_child(path):
+    """Exit status of the battery run on the library at `path` in a child process
+    (0: passed, 1: an assertion failed; a mutant that corrupts memory may also crash
+    the child, which counts as caught without taking the test run down)."""
+    code = ("import sys; sys.path[:0] = [{tests!r}, {root!r}]\n"
+            "import oracle, test_oracle_mutations as m\n"
+            "try:\n    m.battery(oracle.load({path!r}))\nexcept AssertionError:\n    sys.exit(1)\n")
+    here = os.path.dirname(os.path.abspath(__file__))
+    code = code.format(tests=here, root=os.path.dirname(here), path=path)
+    return subprocess.run([sys.executable, "-c", code], capture_output=True, timeout=600).returncode
 
 
 def test_unmutated_passes(tmp_path):
-    battery(_build(tmp_path, "clean", None))
+    path = _build(tmp_path, "clean", None)
+    battery(oracle.load(path))
+    assert _battery_in_child(path) == 0      # the child harness itself works
 
 
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
 def test_mutant_is_caught(tmp_path, name):
-    lib = _build(tmp_path, name, MUTATIONS[name])
-    with pytest.raises(AssertionError):
-        battery(lib)
+    assert _battery_in_child(_build(tmp_path, name, MUTATIONS[name])) != 0
