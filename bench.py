@@ -226,7 +226,7 @@ def time_single(lab, phi, per, reps, flush=None):
 
 def extra_configs(args, peak):
     """The other workloads: 32^3, 256^3 emulsion, the block benchmark sweep at 1024^3, capsule
-    interiors, the uneven batch, the served stream."""
+    interiors, the interior state of moving capsules at 1024^3, the uneven batch, the served stream."""
     import torch
     from paper_1405_1931_gb300 import autotune, fields, hk, serve
     res = {}
@@ -293,6 +293,59 @@ def extra_configs(args, peak):
     res["capsule_interior256"].update({"interior": int((tags == 1).sum()), "exterior": int((tags == 0).sum()),
                                        "undetermined": int((tags == -1).sum())})
     del index, out, res_i
+
+    # Interior state of moving capsules (Sec. 6): the full identification that
+    # initialises or refreshes the state, against the update of the last paragraph of
+    # Sec. 6 (dense, from the whole index field, and from the list of near sites) after
+    # the capsules move by under half a lattice constant.  1024^3, 700 capsules.
+    shape = (1024, 1024, 1024)
+    caps = fields.capsule_params(700, shape, seed=21, a_lo=8.0, a_hi=30.0)
+    assert len(caps) == 700
+    index = torch.from_numpy(fields.capsule_index_field(shape, caps)).cuda()
+    state = lab.interior_state(index)
+    rng = np.random.default_rng(22)
+    caps2 = [((c[0] + d[0], c[1] + d[1], c[2] + d[2]), a)
+             for (c, a), d in zip(caps, rng.uniform(-0.25, 0.25, size=(len(caps), 3)))]
+    I2 = fields.capsule_index_field(shape, caps2)
+    near = ~(I2.reshape(-1) < -0.5)
+    sites = torch.from_numpy(np.flatnonzero(near).astype(np.int32)).cuda()
+    vals = torch.from_numpy(I2.reshape(-1)[near]).cuda()
+    index2 = torch.from_numpy(I2).cuda()
+    del I2, near
+
+    def ev_median(fn, reps=10):
+        ts = []
+        for _ in range(reps):
+            flush_l2(flush)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s0)
+            fn()
+            b.record(s0)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+
+    out_state = torch.empty_like(state)
+    for _ in range(2):
+        lab.interior_state(index, out=out_state)
+    ms_full = ev_median(lambda: lab.interior_state(index, out=out_state))
+    upd = torch.empty_like(state)
+    ms_dense = ev_median(lambda: hk.interior_update(state, index2, out=upd))
+    sp = state.clone()
+    ms_sites = ev_median(lambda: hk.interior_update_sites(sp, sites, vals))
+    full2 = lab.interior_state(index2)
+    assert torch.equal(upd, full2) and torch.equal(sp, full2)     # the update equals a refresh
+    n_int = int((full2 == 1).sum().item())
+    res["capsule_state1024"] = {
+        "workload": "1024^3 index field, 700 capsules (semi-axes U[8,30]), periodic; moved by U[-0.25,0.25] "
+                    "per axis for the update",
+        "refresh_ms": ms_full, "update_dense_ms": ms_dense, "update_sites_ms": ms_sites,
+        "near_sites": int(sites.numel()), "interior_sites": n_int,
+        "refresh_gsites_per_s": 1024 ** 3 / (ms_full * 1e-3) / 1e9,
+        "update_dense_gb_per_s": 1024 ** 3 * 6 / (ms_dense * 1e-3) / 1e9,
+        "cache": "L2 flushed between reps"}
+    del index, index2, state, out_state, upd, sp, full2, sites, vals
+    torch.cuda.empty_cache()
 
     # uneven batch of 96 lattices: per-lattice launches vs one batched launch sequence
     params = fields.batch_params(96, master_seed=2)

@@ -239,6 +239,48 @@ int hk_rc_histogram(const int64_t *sizes, const int64_t *n_clusters, int64_t siz
                     const double *edges, int n_edges, int64_t *hist_out, double *rc_sum_out,
                     int accumulate, void *stream);
 
+/* Interior state of every site of an index field (Sec. 6): the field the
+ * simulation keeps up to date, 1 inside a closed membrane and 0 outside.
+ *   index      device, float[nz][ny][nx]: I < -0.5 far from every membrane, near
+ *              one the signed proximity value (step 2: -d inside, +d outside).
+ *   state_out  device, int8[nz][ny][nx]: a far site (I < -0.5) takes the tag of
+ *              its cluster (steps 3-5, as hk_label_interior: 1 interior, 0
+ *              exterior, -1 undetermined); a near site (any other value, NaN
+ *              included) the side its value names, 1 for I < 0 and 0 otherwise.
+ * This is the full identification the paper uses to initialise the field and to
+ * refresh it from time to time.  The clusters' labels, sizes and tags live in
+ * the context (about 8.5 bytes a site, grown on demand).  Asynchronous on `stream`.
+ * Errors: HK_ERR_ARG, HK_ERR_TOO_LARGE, HK_ERR_NOMEM, HK_ERR_CUDA. */
+int hk_interior_state(hk_ctx *ctx, const float *index, int nx, int ny, int nz, const int periodic[3],
+                      int8_t *state_out, void *stream);
+
+/* The step between refreshes (Sec. 6, last paragraph): for membranes that move
+ * much less than a lattice constant per step, only the sites near a membrane
+ * now change.
+ *   state_prev  device, int8[n_sites]: the previous state (hk_interior_state or
+ *               an earlier update).
+ *   index       device, float[n_sites]: the current index field.
+ *   state_out   device, int8[n_sites]; may be state_prev (in place).
+ * state_out[s] = 1 if I[s] is near and negative, 0 if near and not negative (near:
+ * not I < -0.5), state_prev[s] if far.  A far site keeps its state because a
+ * membrane that moves that slowly cannot carry it across without it being near
+ * now; the tests check the result against hk_interior_state on capsules moving
+ * under half a lattice constant per step.  No context; asynchronous on `stream`.
+ * Errors: HK_ERR_ARG (n_sites < 0, null pointers), HK_ERR_CUDA. */
+int hk_interior_update(const int8_t *state_prev, const float *index, int64_t n_sites, int8_t *state_out,
+                       void *stream);
+
+/* The same step from a list of near sites, as a simulation that walks its
+ * membrane mesh (step 2) produces it: state[sites[i]] = 1 if values[i] < 0, else
+ * 0, for each i < m with values[i] not below -0.5 and 0 <= sites[i] < n_sites
+ * (other entries are skipped); unlisted sites keep their state.  A site listed
+ * twice with values of different sides gets either.  sites (int32) and values
+ * (float) are device arrays of m entries; state is device int8[n_sites],
+ * updated in place.  No context; asynchronous on `stream`.
+ * Errors: HK_ERR_ARG (negative counts, null pointers), HK_ERR_CUDA. */
+int hk_interior_update_sites(int8_t *state, int64_t n_sites, const int32_t *sites, const float *values, int64_t m,
+                             void *stream);
+
 /* Select the tile shape (rows per tile along y and z; x tiles are always 32
  * sites wide).  Supported: (ty, tz) in {(8,8), (16,8), (16,16), (32,8)}; 0,0 =
  * the library default.  Applies to later calls on this context.

@@ -25,6 +25,8 @@ struct hk_ctx {
     size_t ws_bytes = 0;
     void *io = nullptr;       // device buffers of hk_label_host
     size_t io_bytes = 0;
+    void *sbuf = nullptr;     // device buffers of hk_interior_state
+    size_t sbuf_bytes = 0;
     int last_cuda = 0;
     int32_t *dstatus = nullptr;   // device status word (STATUS_* flags), survives workspace growth
     // per-pass timing: a ring of event sets, one per timed call
@@ -53,7 +55,7 @@ constexpr int64_t MAX_SITES = (int64_t)1 << 31;
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t mask, codes, cnt, pre, bsum, face, tinfo, parent, key, psize, xcol, ovf, rootbits, votes, ncl, total;
+    size_t mask, codes, cnt, pre, bsum, face, tinfo, parent, key, psize, xcol, ovf, rootbits, segpre, votes, ncl, total;
 };
 
 // votes_cap > 0: also the root bits and the per-cluster votes of the interior/exterior
@@ -76,6 +78,7 @@ Layout make_layout(const TileInfo &ti, const Plan &P, int64_t votes_cap = 0) {
     L.xcol = take((size_t)P.ntiles * (ti.rows / 32) * 2 * 4);
     L.ovf = take((size_t)P.ntiles * 4);
     L.rootbits = take(votes_cap > 0 ? (size_t)P.nseg * 4 : 0);
+    L.segpre = take(votes_cap > 0 ? (size_t)P.nseg * 4 : 0);
     L.votes = take((size_t)votes_cap * 4);
     L.ncl = take((size_t)hk::MAX_LAT_PER_LAUNCH * 8);
     L.total = off;
@@ -203,8 +206,9 @@ void fold_timing(hk_ctx *ctx, int slot) {
 // (I < -0.5) and, when inside != nullptr, write the interior/exterior tags of its
 // clusters to inside.
 // check_capacity == false: never wait for the counts (the caller compares them).
+// state != nullptr (index fields with inside): also the interior state of every site.
 int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st, bool index_field = false,
-                 int8_t *inside = nullptr, bool check_capacity = true) {
+                 int8_t *inside = nullptr, bool check_capacity = true, int8_t *state = nullptr) {
     TileInfo ti;
     if (!hk::tile_info(ctx->ty, ctx->tz, ti)) return HK_ERR_ARG;
     for (int i = 0; i < n; ++i) {
@@ -299,6 +303,7 @@ int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st, bo
         W.status = ctx->dstatus;
         W.ovf = reinterpret_cast<int32_t *>(base + Ly.ovf);
         W.rootbits = inside ? reinterpret_cast<uint32_t *>(base + Ly.rootbits) : nullptr;
+        W.segpre = inside ? reinterpret_cast<uint32_t *>(base + Ly.segpre) : nullptr;
         W.votes = inside ? reinterpret_cast<int32_t *>(base + Ly.votes) : nullptr;
         W.novf = ctx->dstatus + 1;
         W.piece_cap = P.piece_cap;
@@ -322,7 +327,7 @@ int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st, bo
         e = hk::launch_label(ctx->ty, ctx->tz, dev.data(), cn, P, W, tms.data(), st, ev);
         if (e != cudaSuccess) return fail_cuda(ctx, e);
         if (inside && dev[0].sizes_cap > 0) {
-            e = hk::launch_interior(dev[0], W, st);
+            e = hk::launch_interior(dev[0], W, st, state);
             if (e != cudaSuccess) return fail_cuda(ctx, e);
         }
         if (chunk_check) {
@@ -405,6 +410,7 @@ void hk_destroy(hk_ctx *ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->io) cudaFree(ctx->io);
+    if (ctx->sbuf) cudaFree(ctx->sbuf);
     if (ctx->dstatus) cudaFree(ctx->dstatus);
     drop_graphs(ctx);
     for (auto &set : ctx->ev)
@@ -460,6 +466,54 @@ int hk_label_interior(hk_ctx *ctx, const float *index, int nx, int ny, int nz, c
     l.hist = hist_out;
     l.n_clusters = n_clusters_out;
     return run_lattices(ctx, &l, 1, static_cast<cudaStream_t>(stream), true, sizes_cap > 0 ? inside_out : nullptr);
+}
+
+int hk_interior_state(hk_ctx *ctx, const float *index, int nx, int ny, int nz, const int periodic[3],
+                      int8_t *state_out, void *stream) {
+    if (!ctx || !periodic || !index || !state_out) return HK_ERR_ARG;
+    if (nx < 1 || ny < 1 || nz < 1) return HK_ERR_ARG;
+    const int64_t N = (int64_t)nx * ny * nz;
+    if (N >= MAX_SITES) return HK_ERR_TOO_LARGE;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return fail_cuda(ctx, e);
+    // labels, sizes, histogram, count and tags of the far sites' clusters, in the
+    // context; ceil(N / 2) clusters always fit
+    const int64_t cap = (N + 1) / 2;
+    const size_t o_lab = 0, o_sizes = align256(4 * N), o_hist = o_sizes + align256(8 * cap);
+    const size_t o_ncl = o_hist + 256, o_inside = o_ncl + 256, need = o_inside + align256(cap);
+    if (need > ctx->sbuf_bytes) {
+        if (ctx->sbuf) { cudaDeviceSynchronize(); cudaFree(ctx->sbuf); ctx->sbuf = nullptr; ctx->sbuf_bytes = 0; }
+        if (cudaMalloc(&ctx->sbuf, need) != cudaSuccess) { cudaGetLastError(); return HK_ERR_NOMEM; }
+        ctx->sbuf_bytes = need;
+    }
+    char *b = static_cast<char *>(ctx->sbuf);
+    hk_lattice l;
+    l.phi = index;
+    l.nx = nx; l.ny = ny; l.nz = nz;
+    for (int a = 0; a < 3; ++a) l.periodic[a] = periodic[a];
+    l.labels = reinterpret_cast<int32_t *>(b + o_lab);
+    l.sizes = reinterpret_cast<int64_t *>(b + o_sizes);
+    l.sizes_cap = cap;
+    l.hist = reinterpret_cast<int64_t *>(b + o_hist);
+    l.n_clusters = reinterpret_cast<int64_t *>(b + o_ncl);
+    return run_lattices(ctx, &l, 1, static_cast<cudaStream_t>(stream), true, reinterpret_cast<int8_t *>(b + o_inside),
+                        false, state_out);
+}
+
+int hk_interior_update(const int8_t *state_prev, const float *index, int64_t n_sites, int8_t *state_out,
+                       void *stream) {
+    if (n_sites < 0 || (n_sites > 0 && (!state_prev || !index || !state_out))) return HK_ERR_ARG;
+    const cudaError_t e = hk::launch_interior_update(state_prev, index, n_sites, state_out,
+                                                     static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? HK_OK : HK_ERR_CUDA;
+}
+
+int hk_interior_update_sites(int8_t *state, int64_t n_sites, const int32_t *sites, const float *values, int64_t m,
+                             void *stream) {
+    if (n_sites < 0 || m < 0 || (m > 0 && (!state || !sites || !values))) return HK_ERR_ARG;
+    const cudaError_t e = hk::launch_interior_update_sites(state, n_sites, sites, values, m,
+                                                           static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? HK_OK : HK_ERR_CUDA;
 }
 
 int hk_label_batched(hk_ctx *ctx, const hk_lattice *lats, int n, void *stream) {

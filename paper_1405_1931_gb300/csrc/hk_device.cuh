@@ -68,6 +68,7 @@ struct Work {
                         // (x = lastX) column, one bit per tile row
     int32_t *status;    // [1] device-side error flags (STATUS_*), owned by the context
     uint32_t *rootbits; // [nseg] cluster-root run starts of each row segment (index fields only)
+    uint32_t *segpre;   // [nseg] clusters ranked before each row segment (index fields only)
     int32_t *votes;     // [sizes_cap] sign votes per cluster (index fields only)
     int32_t *ovf;       // [ntiles] tiles with more runs than the fast tile pass holds
     int32_t *novf;      // [1] entries of ovf (reset by the occupancy pass of every call)

@@ -976,13 +976,26 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapBa
 // occ_mode 1: every face pair (cluster site, near site) votes with the sign of I at
 // the near site; a cluster with more negative votes is interior.  One lattice.
 // --------------------------------------------------------------------------------------
-// Rank (compacted id - 1) of the cluster whose first site is `lab`: roots of the
-// earlier rows, of the earlier segments of its row and of its segment before it.
+// Clusters ranked before each row segment of an index field: the roots of the
+// lattice's earlier rows and of the row's earlier segments.  One thread per row.
+__global__ void __launch_bounds__(256) k_segpre(const LatDev L, Work W) {
+    const int64_t rows = (int64_t)L.ny * L.nz;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < rows; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t rowseg = L.seg0 + q * L.nbx;
+        uint32_t acc = W.pre[L.row0 + q] - W.pre[L.row0];
+        for (int b = 0; b < L.nbx; ++b) {
+            W.segpre[rowseg + b] = acc;
+            acc += W.cnt[rowseg + b];
+        }
+    }
+}
+
+// Rank (compacted id - 1) of the cluster whose first site is `lab`: the clusters
+// ranked before its segment and the roots of its segment before it.
 __device__ __forceinline__ int64_t rank_of_root(const LatDev &L, const Work &W, int lab) {
-    const int x = lab % L.nx, q = lab / L.nx;
-    const int64_t rowseg = L.seg0 + (int64_t)q * L.nbx;
-    return (int64_t)(uint32_t)(W.pre[L.row0 + q] - W.pre[L.row0]) + bytes_sum(W.cnt, rowseg, x >> 5) +
-           __popc(W.rootbits[rowseg + (x >> 5)] & ((1u << (x & 31)) - 1u));
+    const int q = lab / L.nx, x = lab - q * L.nx;
+    const int64_t seg = L.seg0 + (int64_t)q * L.nbx + (x >> 5);
+    return (int64_t)W.segpre[seg] + __popc(W.rootbits[seg] & ((1u << (x & 31)) - 1u));
 }
 
 __global__ void __launch_bounds__(256) k_votes_clear(const LatDev L, Work W) {
@@ -996,37 +1009,40 @@ __global__ void __launch_bounds__(256) k_votes_clear(const LatDev L, Work W) {
 // fluid, collect most votes); higher ranks go straight to global memory.
 constexpr int VOTE_SMEM = 1024;
 
+// The votes of near site s (value v): one per face neighbour that is a cluster site.
+__device__ __forceinline__ void vote_site(const LatDev &L, const Work &W, int64_t s, float v, int *sv) {
+    if (!(v >= -0.5f)) return;                 // a cluster site (or NaN): not a near site
+    const int sign = v < 0.0f ? -1 : (v > 0.0f ? 1 : 0);
+    if (sign == 0) return;
+    const int dims[3] = {L.nx, L.ny, L.nz};
+    const int x = (int)(s % L.nx);
+    const int64_t q = s / L.nx;
+    const int y = (int)(q % L.ny), z = (int)(q / L.ny);
+#pragma unroll
+    for (int dir = 0; dir < 6; ++dir) {
+        const int axis = dir >> 1;
+        int c[3] = {x, y, z};
+        c[axis] += (dir & 1) ? 1 : -1;
+        if (c[axis] < 0 || c[axis] >= dims[axis]) {
+            if (!L.per[axis]) continue;
+            c[axis] = c[axis] < 0 ? dims[axis] - 1 : 0;
+        }
+        const int lab = L.labels[c[0] + (int64_t)L.nx * (c[1] + (int64_t)L.ny * c[2])];
+        if (lab < 0) continue;
+        const int64_t k = rank_of_root(L, W, lab);
+        if (k >= L.sizes_cap) continue;
+        if (k < VOTE_SMEM) atomicAdd(&sv[k], sign);
+        else atomicAdd(W.votes + k, sign);
+    }
+}
+
 __global__ void __launch_bounds__(256) k_votes(const LatDev L, Work W) {
     __shared__ int sv[VOTE_SMEM];
     for (int i = threadIdx.x; i < VOTE_SMEM; i += blockDim.x) sv[i] = 0;
     __syncthreads();
     const int64_t N = (int64_t)L.nx * L.ny * L.nz;
-    const int dims[3] = {L.nx, L.ny, L.nz};
-    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
-        const float v = L.phi[s];
-        if (!(v >= -0.5f)) continue;              // a cluster site (or NaN): not a near site
-        const int sign = v < 0.0f ? -1 : (v > 0.0f ? 1 : 0);
-        if (sign == 0) continue;
-        const int x = (int)(s % L.nx);
-        const int64_t q = s / L.nx;
-        const int y = (int)(q % L.ny), z = (int)(q / L.ny);
-#pragma unroll
-        for (int dir = 0; dir < 6; ++dir) {
-            const int axis = dir >> 1;
-            int c[3] = {x, y, z};
-            c[axis] += (dir & 1) ? 1 : -1;
-            if (c[axis] < 0 || c[axis] >= dims[axis]) {
-                if (!L.per[axis]) continue;
-                c[axis] = c[axis] < 0 ? dims[axis] - 1 : 0;
-            }
-            const int lab = L.labels[c[0] + (int64_t)L.nx * (c[1] + (int64_t)L.ny * c[2])];
-            if (lab < 0) continue;
-            const int64_t k = rank_of_root(L, W, lab);
-            if (k >= L.sizes_cap) continue;
-            if (k < VOTE_SMEM) atomicAdd(&sv[k], sign);
-            else atomicAdd(W.votes + k, sign);
-        }
-    }
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x)
+        vote_site(L, W, s, L.phi[s], sv);
     __syncthreads();
     for (int i = threadIdx.x; i < VOTE_SMEM; i += blockDim.x)
         if (sv[i]) atomicAdd(W.votes + i, sv[i]);
@@ -1040,7 +1056,64 @@ __global__ void __launch_bounds__(256) k_inside(const LatDev L, Work W) {
     }
 }
 
-cudaError_t launch_interior(const LatDev &L, const Work &W, cudaStream_t st) {
+// Interior state of every site (Sec. 6: 1 far inside, 0 far outside): a far site
+// (I < -0.5) takes its cluster's tag, a near site the side its value names (step 2:
+// -d inside, +d outside), 1 for I < 0 and 0 otherwise.  Two passes: each cluster's
+// first site (labels[s] == s) gets the tag of its rank, then every far site copies the
+// tag from its label's site.  Near sites are never a cluster's first site, so the
+// second pass only rewrites first sites with the value they hold.
+__device__ __forceinline__ void state_root(const LatDev &L, const Work &W, int8_t *state, int64_t s, int lab) {
+    if (lab != s) return;
+    const int64_t k = rank_of_root(L, W, (int)s);
+    state[s] = k < L.sizes_cap ? L.inside[k] : (int8_t)-1;
+}
+
+// vec: labels 16-byte aligned, 4 sites at a time
+__global__ void __launch_bounds__(256) k_state_roots(const LatDev L, Work W, int8_t *state, bool vec) {
+    const int64_t N = (int64_t)L.nx * L.ny * L.nz;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t done = 0;
+    if (vec) {
+        for (int64_t i = t0; i < N / 4; i += stride) {
+            const int4 lb = __ldcs(reinterpret_cast<const int4 *>(L.labels) + i);
+            state_root(L, W, state, 4 * i, lb.x);
+            state_root(L, W, state, 4 * i + 1, lb.y);
+            state_root(L, W, state, 4 * i + 2, lb.z);
+            state_root(L, W, state, 4 * i + 3, lb.w);
+        }
+        done = N / 4 * 4;
+    }
+    for (int64_t s = done + t0; s < N; s += stride) state_root(L, W, state, s, L.labels[s]);
+}
+
+__device__ __forceinline__ uint32_t state_byte(const int8_t *state, float v, int lab) {
+    if (v < -0.5f) return (uint32_t)(uint8_t)state[lab];
+    return v < 0.0f ? 1u : 0u;
+}
+
+// vec: phi, labels and state 16-byte aligned, 16 sites at a time (one 16-byte store)
+__global__ void __launch_bounds__(256) k_state(const LatDev L, int8_t *state, bool vec) {
+    const int64_t N = (int64_t)L.nx * L.ny * L.nz;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t done = 0;
+    if (vec) {
+        for (int64_t i = t0; i < N / 16; i += stride) {
+            uint32_t w[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 v = __ldcs(reinterpret_cast<const float4 *>(L.phi) + 4 * i + q);
+                const int4 lb = __ldcs(reinterpret_cast<const int4 *>(L.labels) + 4 * i + q);
+                w[q] = state_byte(state, v.x, lb.x) | (state_byte(state, v.y, lb.y) << 8) |
+                       (state_byte(state, v.z, lb.z) << 16) | (state_byte(state, v.w, lb.w) << 24);
+            }
+            reinterpret_cast<int4 *>(state)[i] = make_int4((int)w[0], (int)w[1], (int)w[2], (int)w[3]);
+        }
+        done = N / 16 * 16;
+    }
+    for (int64_t s = done + t0; s < N; s += stride) state[s] = (int8_t)state_byte(state, L.phi[s], L.labels[s]);
+}
+
+cudaError_t launch_interior(const LatDev &L, const Work &W, cudaStream_t st, int8_t *state) {
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -1049,8 +1122,89 @@ cudaError_t launch_interior(const LatDev &L, const Work &W, cudaStream_t st) {
     if (gv > (int64_t)nsm * 16) gv = (int64_t)nsm * 16;
     const unsigned gc = (unsigned)(nsm > 0 ? nsm * 4 : 1);
     k_votes_clear<<<gc, 256, 0, st>>>(L, W);
+    auto a16 = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+    const int64_t rows = (int64_t)L.ny * L.nz;
+    k_segpre<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(L, W);
     k_votes<<<(unsigned)(gv > 0 ? gv : 1), 256, 0, st>>>(L, W);
     k_inside<<<gc, 256, 0, st>>>(L, W);
+    if (state) {
+        k_state_roots<<<(unsigned)(gv > 0 ? gv : 1), 256, 0, st>>>(L, W, state, a16(L.labels));
+        k_state<<<(unsigned)(gv > 0 ? gv : 1), 256, 0, st>>>(L, state, a16(L.phi) && a16(L.labels) && a16(state));
+    }
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------------------
+// Interior state of slowly moving membranes (Sec. 6, last paragraph): only the sites
+// near a membrane now change, to the side their value names; every other site keeps
+// its state.
+// --------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t update_byte(uint32_t w, int b, float v) {
+    const uint32_t side = v < 0.0f ? 1u : 0u;
+    return (v < -0.5f) ? w : ((w & ~(0xffu << (8 * b))) | (side << (8 * b)));
+}
+
+// Dense form.  vec: all three arrays 16-byte aligned; then 16 sites per step, one
+// 16-byte state load and store and four 16-byte index loads.
+__global__ void __launch_bounds__(256) k_interior_update(const int8_t *prev, const float *index, int64_t n,
+                                                          int8_t *out, bool vec) {
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t done = 0;
+    if (vec) {
+        const int64_t nv = n / 16;
+        for (int64_t i = t0; i < nv; i += stride) {
+            const int4 sp = __ldcs(reinterpret_cast<const int4 *>(prev) + i);
+            uint32_t w[4] = {(uint32_t)sp.x, (uint32_t)sp.y, (uint32_t)sp.z, (uint32_t)sp.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 v = __ldcs(reinterpret_cast<const float4 *>(index) + 4 * i + q);
+                w[q] = update_byte(w[q], 0, v.x);
+                w[q] = update_byte(w[q], 1, v.y);
+                w[q] = update_byte(w[q], 2, v.z);
+                w[q] = update_byte(w[q], 3, v.w);
+            }
+            __stcs(reinterpret_cast<int4 *>(out) + i, make_int4((int)w[0], (int)w[1], (int)w[2], (int)w[3]));
+        }
+        done = nv * 16;
+    }
+    for (int64_t s = done + t0; s < n; s += stride) {
+        const float v = index[s];
+        out[s] = (v < -0.5f) ? prev[s] : (int8_t)(v < 0.0f ? 1 : 0);
+    }
+}
+
+// Sparse form: the caller lists the near sites with their values.
+__global__ void __launch_bounds__(256) k_interior_update_sites(int8_t *state, int64_t n, const int32_t *sites,
+                                                                const float *values, int64_t m) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = sites[i];
+        const float v = values[i];
+        if (s >= 0 && s < n && !(v < -0.5f)) state[s] = (int8_t)(v < 0.0f ? 1 : 0);
+    }
+}
+
+static unsigned stream_grid(int64_t units) {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int64_t g = (units + 255) / 256;
+    const int64_t cap = (int64_t)(nsm > 0 ? nsm : 1) * 8;
+    if (g > cap) g = cap;
+    return (unsigned)(g > 0 ? g : 1);
+}
+
+cudaError_t launch_interior_update(const int8_t *prev, const float *index, int64_t n, int8_t *out, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const bool vec = ((reinterpret_cast<uintptr_t>(prev) | reinterpret_cast<uintptr_t>(index) |
+                       reinterpret_cast<uintptr_t>(out)) & 15) == 0;
+    k_interior_update<<<stream_grid(vec ? n / 16 + 1 : n), 256, 0, st>>>(prev, index, n, out, vec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_interior_update_sites(int8_t *state, int64_t n, const int32_t *sites, const float *values,
+                                         int64_t m, cudaStream_t st) {
+    if (m <= 0) return cudaSuccess;
+    k_interior_update_sites<<<stream_grid(m), 256, 0, st>>>(state, n, sites, values, m);
     return cudaGetLastError();
 }
 

@@ -42,7 +42,14 @@ cudaError_t launch_label(int ty, int tz, const LatDev *lats, int n, const Plan &
 
 // Interior/exterior tags of a lattice labelled with occ_mode 1 (after launch_label on
 // the same stream; needs W.rootbits and W.votes).
-cudaError_t launch_interior(const LatDev &L, const Work &W, cudaStream_t st);
+// state != nullptr: also the interior state of every site
+cudaError_t launch_interior(const LatDev &L, const Work &W, cudaStream_t st, int8_t *state = nullptr);
+// out[s] = the side index[s] names where the site is near a membrane (index >= -0.5 or
+// NaN), else prev[s]; out may be prev
+cudaError_t launch_interior_update(const int8_t *prev, const float *index, int64_t n, int8_t *out, cudaStream_t st);
+// state[sites[i]] = the side values[i] names, for near values and sites in [0, n)
+cudaError_t launch_interior_update_sites(int8_t *state, int64_t n, const int32_t *sites, const float *values,
+                                         int64_t m, cudaStream_t st);
 // dst[i] = src[i] for i < min(*count, cap): a copy sized on the device (dst may be
 // device-accessible host memory)
 cudaError_t launch_copy_counted(const int64_t *src, const int64_t *count, int64_t cap, int64_t *dst,

@@ -108,6 +108,7 @@ extern "C" int hk_label_noalloc(const float *phi, int nx, int ny, int nz, const 
     W.status = reinterpret_cast<int32_t *>(base + c.status);
     W.ovf = reinterpret_cast<int32_t *>(base + c.ovf);
     W.rootbits = nullptr;   // no interior/exterior identification here
+    W.segpre = nullptr;
     W.votes = nullptr;
     W.novf = W.status + 1;
     W.piece_cap = P.piece_cap;

@@ -212,33 +212,38 @@ def capsule_params(n: int, shape: tuple, seed: int, a_lo: float = 6.0, a_hi: flo
 def capsule_index_field(shape: tuple, capsules) -> np.ndarray:
     """Index field I of Sec. 6 (steps 1-2) for closed ellipsoidal membranes.
 
-    For capsule c, F_c(x) = sum_i ((x_i - c_i) / a_i)^2 (float64).  Sites with
-    F_c <= 1 and a 6-neighbour F_c > 1 form the inner layer (I = -0.25), sites
-    with F_c > 1 and a 6-neighbour F_c <= 1 the outer layer (I = +0.25); every
-    other site is far (I = -1).  The two layers close around each capsule, so
-    they separate its interior from the exterior.  Capsules must stay clear of
-    each other and of the box faces (``capsule_params`` ensures both).
+    For capsule c, F_c(x) = sum_i ((x_i - c_i) / a_i)^2 (float64, summed z, y, x).
+    Sites with F_c <= 1 and a 6-neighbour F_c > 1 form the inner layer
+    (I = -0.25), sites with F_c > 1 and a 6-neighbour F_c <= 1 the outer layer
+    (I = +0.25); every other site is far (I = -1).  The two layers close around
+    each capsule, so they separate its interior from the exterior.  Capsules must
+    stay clear of each other and of the box faces (``capsule_params`` ensures
+    both).  F_c is evaluated only on the capsule's bounding box grown by two
+    sites: beyond it F_c > 1 at a site and at all its neighbours.
     """
     nz, ny, nx = shape
     I = np.full(shape, INDEX_FAR, dtype=np.float32)
-    z = np.arange(-1, nz + 1, dtype=np.float64)
-    y = np.arange(-1, ny + 1, dtype=np.float64)
-    x = np.arange(-1, nx + 1, dtype=np.float64)
-    nbs = ((slice(0, -2), slice(1, -1), slice(1, -1)), (slice(2, None), slice(1, -1), slice(1, -1)),
-           (slice(1, -1), slice(0, -2), slice(1, -1)), (slice(1, -1), slice(2, None), slice(1, -1)),
-           (slice(1, -1), slice(1, -1), slice(0, -2)), (slice(1, -1), slice(1, -1), slice(2, None)))
     for (cx, cy, cz), (ax, ay, az) in capsules:
+        lo = [max(0, int(np.floor(c - a)) - 2) for c, a in ((cz, az), (cy, ay), (cx, ax))]
+        hi = [min(n, int(np.ceil(c + a)) + 3) for c, a, n in ((cz, az, nz), (cy, ay, ny), (cx, ax, nx))]
+        # coordinates of the box and one site around it (the neighbours of its sites)
+        z = np.arange(lo[0] - 1, hi[0] + 1, dtype=np.float64)
+        y = np.arange(lo[1] - 1, hi[1] + 1, dtype=np.float64)
+        x = np.arange(lo[2] - 1, hi[2] + 1, dtype=np.float64)
         F = (((z - cz) / az) ** 2)[:, None, None] + (((y - cy) / ay) ** 2)[None, :, None] \
             + (((x - cx) / ax) ** 2)[None, None, :]
         inside = F <= 1.0
         core = inside[1:-1, 1:-1, 1:-1]
         any_out = np.zeros_like(core)
         any_in = np.zeros_like(core)
-        for sl in nbs:
+        for sl in ((slice(0, -2), slice(1, -1), slice(1, -1)), (slice(2, None), slice(1, -1), slice(1, -1)),
+                   (slice(1, -1), slice(0, -2), slice(1, -1)), (slice(1, -1), slice(2, None), slice(1, -1)),
+                   (slice(1, -1), slice(1, -1), slice(0, -2)), (slice(1, -1), slice(1, -1), slice(2, None))):
             any_out |= ~inside[sl]
             any_in |= inside[sl]
-        I[~core & any_in] = INDEX_OUTER
-        I[core & any_out] = INDEX_INNER
+        box = I[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]]
+        box[~core & any_in] = INDEX_OUTER
+        box[core & any_out] = INDEX_INNER
     return I
 
 

@@ -21,7 +21,8 @@ HK_ERR_CUDA, HK_ERR_TIMEOUT, HK_ERR_NOMEM = 4, 5, 6
 
 EXPORTED = ("hk_create", "hk_destroy", "hk_workspace_bytes", "hk_reserve", "hk_label", "hk_label_batched",
             "hk_label_host", "hk_label_host_async", "hk_set_tile", "hk_set_timing", "hk_get_timing", "hk_sync_status", "hk_set_graphs", "hk_last_cuda_error", "hk_strerror", "hk_label_noalloc",
-            "hk_label_interior", "hk_rc_histogram",
+            "hk_label_interior", "hk_rc_histogram", "hk_interior_state", "hk_interior_update",
+            "hk_interior_update_sites",
             "hk_gen_iid", "hk_gen_spheres", "hk_gen_spheres_dev", "hk_gen_capsule")
 
 _lock = threading.Lock()
@@ -66,6 +67,9 @@ def load():
             "hk_label_noalloc": (I, [P, I, I, I, P, P, P, I64, P, P, P]),
             "hk_label_interior": (I, [P, P, I, I, I, P, P, P, I64, P, P, P, P]),
             "hk_rc_histogram": (I, [P, P, I64, P, I, P, P, I, P]),
+            "hk_interior_state": (I, [P, P, I, I, I, P, P, P]),
+            "hk_interior_update": (I, [P, P, I64, P, P]),
+            "hk_interior_update_sites": (I, [P, I64, P, P, I64, P]),
             "hk_set_tile": (I, [P, I, I]),
             "hk_set_timing": (I, [P, I]),
             "hk_set_graphs": (I, [P, I]),
@@ -154,6 +158,18 @@ def hk_label_host(ctx, phi_host, nx, ny, nz, periodic, labels_host, sizes_host, 
                   n_clusters_host, stream=0) -> int:
     return load().hk_label_host(ctx, phi_host, nx, ny, nz, _per(periodic), labels_host, sizes_host,
                                 int(sizes_cap), hist_host, n_clusters_host, stream)
+
+
+def hk_interior_state(ctx, index, nx, ny, nz, periodic, state_out, stream=0) -> int:
+    return load().hk_interior_state(ctx, index, nx, ny, nz, _per(periodic), state_out, stream)
+
+
+def hk_interior_update(state_prev, index, n_sites, state_out, stream=0) -> int:
+    return load().hk_interior_update(state_prev, index, int(n_sites), state_out, stream)
+
+
+def hk_interior_update_sites(state, n_sites, sites, values, m, stream=0) -> int:
+    return load().hk_interior_update_sites(state, int(n_sites), sites, values, int(m), stream)
 
 
 def hk_label_host_async(ctx, phi_host, nx, ny, nz, periodic, labels_host, sizes_host, sizes_cap, hist_host,
@@ -324,6 +340,18 @@ class Labeller:
             raise HKError(rc, "hk_label_interior")
         return labels, sizes, hist, ncl, inside
 
+    def interior_state(self, index, periodic=(1, 1, 1), out=None, stream=None):
+        """Sec. 6: the interior state of every site (int8: 1 inside, 0 outside, -1 undetermined)."""
+        import torch
+        if not (index.is_cuda and index.dtype == torch.float32 and index.dim() == 3 and index.is_contiguous()):
+            raise ValueError("index must be a contiguous float32 CUDA tensor of shape (nz, ny, nx)")
+        nz, ny, nx = index.shape
+        state = torch.empty(index.shape, dtype=torch.int8, device=index.device) if out is None else out
+        rc = hk_interior_state(self.ctx, index.data_ptr(), nx, ny, nz, periodic, state.data_ptr(), _stream_handle(stream))
+        if rc != HK_OK:
+            raise HKError(rc, "hk_interior_state")
+        return state
+
     def label_batched(self, items, stream=None, check=True):
         """items: list of (phi, periodic, (labels, sizes, hist, ncl, cap)) with CUDA tensors."""
         lats = []
@@ -363,3 +391,26 @@ class Labeller:
                                  _stream_handle(stream))
         if rc != HK_OK:
             raise HKError(rc, "hk_label_host_async")
+
+
+def interior_update(state_prev, index, out=None, stream=None):
+    """Sec. 6, last paragraph: near sites take their side now, far sites keep their state
+    (CUDA tensors; out may be state_prev)."""
+    if state_prev.shape != index.shape or not (state_prev.is_contiguous() and index.is_contiguous()):
+        raise ValueError("state_prev and index must be contiguous tensors of one shape")
+    out = state_prev if out is None else out
+    rc = hk_interior_update(state_prev.data_ptr(), index.data_ptr(), index.numel(), out.data_ptr(), _stream_handle(stream))
+    if rc != HK_OK:
+        raise HKError(rc, "hk_interior_update")
+    return out
+
+
+def interior_update_sites(state, sites, values, stream=None):
+    """The same step from a list of near sites (int32) and their values (float32), in place."""
+    if sites.numel() != values.numel():
+        raise ValueError("sites and values must have one length")
+    rc = hk_interior_update_sites(state.data_ptr(), state.numel(), sites.data_ptr(), values.data_ptr(), sites.numel(),
+                                  _stream_handle(stream))
+    if rc != HK_OK:
+        raise HKError(rc, "hk_interior_update_sites")
+    return state

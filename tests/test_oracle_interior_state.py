@@ -89,3 +89,27 @@ def test_update_rule_by_hand():
     # far sites keep their state (1, 0, -1); near sites take their side: +0.25 -> 0,
     # -0.25 -> 1, 0 -> 0, NaN -> 0
     assert oracle.interior_update(state, index).reshape(-1).tolist() == [1, 0, -1, 0, 1, 0, 0]
+
+
+@pytest.mark.parametrize("seed", [0, 5])
+def test_capsule_generator_layers_from_their_definition(seed):
+    """The input generator (evaluated on bounding boxes) puts the inner layer exactly on
+    the inside sites with an outside 6-neighbour and the outer layer on the outside
+    sites with an inside 6-neighbour, judged on the whole grid."""
+    shape = (60, 52, 70)
+    caps = fields.capsule_params(6, shape, seed=seed, a_lo=4.0, a_hi=14.0)
+    I = fields.capsule_index_field(shape, caps)
+    ind = inside_indicator(shape, caps).astype(bool)
+    pad = np.pad(ind, 1, mode="constant", constant_values=False)
+    nb_out = np.zeros(shape, dtype=bool)
+    nb_in = np.zeros(shape, dtype=bool)
+    for axis in range(3):
+        for d in (-1, 1):
+            sl = [slice(1, -1)] * 3
+            sl[axis] = slice(1 + d, pad.shape[axis] - 1 + d)
+            nb_in |= pad[tuple(sl)]
+            nb_out |= ~pad[tuple(sl)]
+    want = np.full(shape, fields.INDEX_FAR, dtype=np.float32)
+    want[~ind & nb_in] = fields.INDEX_OUTER
+    want[ind & nb_out] = fields.INDEX_INNER
+    np.testing.assert_array_equal(I, want)
