@@ -71,6 +71,12 @@ TRAFFIC_SITES = 512 ** 3
 TRAFFIC_BYTES = {"occupancy": 554.3e6, "tile_label": 63.9e6, "face_merge": 37.2e6, "piece_finalize": 30.0e6,
                  "scan": 8.5e6, "lattice_finish": 0.0, "flatten": 629.0e6}
 TRAFFIC_SOURCE_SHA = "1923cd4e49ec9fb9"
+# Warp instructions of one launch of the two instruction-bound passes at 512^3
+# (smsp__inst_executed.sum of one ncu capture; the summary with its command is
+# profiles/hk_label_kernels_critical512_full.md), scaled by sites like the traffic and
+# held to the same kernel sources.  Their roofline is the issue rate: 4 warp
+# schedulers per SM, each issuing at most one warp instruction per clock.
+INST_PER_LAUNCH = {"tile_label": 391956508, "flatten": 200328399}
 
 
 def kernel_source_sha() -> str:
@@ -489,12 +495,23 @@ def main():
                         "achieved_gbs": (b / (ms * 1e-3) / 1e9) if b else 0.0,
                         "frac": (b / (ms * 1e-3) / 1e9 / peak) if b else 0.0,
                         "traffic": TRAFFIC_BYTES[name] * N / TRAFFIC_SITES if traffic_ok else None})
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    clk_mhz = clk.get("sm_max_mhz") or 2070.0
+    issue_peak = nsm * 4 * clk_mhz * 1e6 / 1e9                  # G warp instructions / s
+    for k in kernels:
+        if k["kernel"] in INST_PER_LAUNCH:
+            inst = INST_PER_LAUNCH[k["kernel"]] * N / TRAFFIC_SITES if traffic_ok else None
+            ach = inst / (k["avg_ms"] * 1e-3) / 1e9 if inst else None
+            k["issue"] = {"bound": "alu", "unit": "G warp-instr/s", "achieved": ach, "peak": issue_peak,
+                          "frac": ach / issue_peak if ach else None, "warp_instructions": inst,
+                          "peak_basis": f"{nsm} SMs x 4 schedulers x 1 warp instruction per clock x {clk_mhz:.0f} MHz"}
     dom = max(kernels, key=lambda k: k["avg_ms"])
     path_traffic = sum(TRAFFIC_BYTES.values()) * N / TRAFFIC_SITES if traffic_ok else None
     roofline = {"bound": "hbm", "unit": "GB/s", "achieved": path_achieved, "peak": peak,
                 "frac": path_achieved / peak, "traffic": path_traffic, "peak_kind": peak_kind,
                 "scope": "one hk_label call (all passes)", "algorithmic_bytes": path_bytes,
-                "dominant_kernel": dom["kernel"], "dominant_share": dom["share"]}
+                "dominant_kernel": dom["kernel"], "dominant_share": dom["share"],
+                "dominant_kernel_issue": dom.get("issue")}
 
     # End to end through the host-buffer entry points, every step's copy of phi in and
     # of labels, sizes, histogram and count out inside the timed region.  The headline
