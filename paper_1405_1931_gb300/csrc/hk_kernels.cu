@@ -18,6 +18,7 @@
 //                     (staged in shared memory, TMA tensor stores), the sizes
 //                     in label order and the histogram.
 #include <cstring>
+#include <mutex>
 
 #include "hk_device.cuh"
 #include "hk_launch.h"
@@ -1264,31 +1265,43 @@ static cudaError_t launch_all(const LatDev *lats, int n, const Plan &P, const Wo
     const size_t smem1 = sizeof(LabelSmem<TY, TZ, CAP1>), smem1b = sizeof(LabelSmem<TY, TZ, CAP1B>);
     const size_t smem4 = sizeof(FlatSmem<TY, TZ>);
     cudaError_t e;
-    static int grid4 = 0, grid1b = 0;
-    if (!grid4) {
-        e = cudaFuncSetAttribute(k_tile_label<TY, TZ, NL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem1);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_tile_label<TY, TZ, NL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem1b);
-        if (e != cudaSuccess) return e;
-        grid1b = persistent_grid(k_tile_label<TY, TZ, NL, false>, SH::NT, smem1b, INT32_MAX);
-        e = cudaFuncSetAttribute(k_flatten<TY, TZ, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4);
-        if (e != cudaSuccess) return e;
-        grid4 = persistent_grid(k_flatten<TY, TZ, NL>, SH::NT, smem4, INT32_MAX);
+    // Once per device a process uses: the shared-memory opt-ins (a device attribute of
+    // each kernel) and the resident-CTA counts of the persistent passes.
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+    static std::mutex init_mu;
+    static int grid_cache[MAX_DEVICES][3];          // tile pass over dense tiles, flatten, TMA occupancy
+    const size_t smem0 = sizeof(OccSmem<TY, TZ>);
+    int grid1b, grid4, grid0;
+    {
+        std::lock_guard<std::mutex> init_lock(init_mu);
+        int *c = grid_cache[dev];
+        if (!c[1]) {
+            e = cudaFuncSetAttribute(k_tile_label<TY, TZ, NL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem1);
+            if (e != cudaSuccess) return e;
+            e = cudaFuncSetAttribute(k_tile_label<TY, TZ, NL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem1b);
+            if (e != cudaSuccess) return e;
+            e = cudaFuncSetAttribute(k_flatten<TY, TZ, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4);
+            if (e != cudaSuccess) return e;
+            e = cudaFuncSetAttribute(k_occupancy_tma<TY, TZ, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem0);
+            if (e != cudaSuccess) return e;
+            c[0] = persistent_grid(k_tile_label<TY, TZ, NL, false>, SH::NT, smem1b, INT32_MAX);
+            c[2] = persistent_grid(k_occupancy_tma<TY, TZ, NL>, 256, smem0, INT32_MAX);
+            c[1] = persistent_grid(k_flatten<TY, TZ, NL>, SH::NT, smem4, INT32_MAX);
+        }
+        grid1b = c[0];
+        grid4 = c[1];
+        grid0 = c[2];
     }
     const unsigned g4 = (unsigned)(P.ntiles < grid4 ? P.ntiles : grid4);
     auto mark = [&](int i) { if (ev) cudaEventRecord(ev[i], st); };
     mark(0);
     if (all_tma) {
-        static int grid0 = 0;
-        const size_t smem0 = sizeof(OccSmem<TY, TZ>);
-        if (!grid0) {
-            e = cudaFuncSetAttribute(k_occupancy_tma<TY, TZ, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem0);
-            if (e != cudaSuccess) return e;
-            grid0 = persistent_grid(k_occupancy_tma<TY, TZ, NL>, 256, smem0, INT32_MAX);
-        }
         const unsigned g0 = (unsigned)(P.ntiles < grid0 ? P.ntiles : grid0);
         k_occupancy_tma<TY, TZ, NL><<<g0, 256, smem0, st>>>(TB, B, W, P.ntiles);
     } else {

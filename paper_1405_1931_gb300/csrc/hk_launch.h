@@ -14,6 +14,8 @@ struct TmapPair;
 // lattices per launch: the descriptors and tensor maps of a launch travel as kernel
 // parameters (under the 32 KB parameter limit)
 constexpr int MAX_LAT_PER_LAUNCH = 64;
+// devices one process may use (per-device launch state is kept for this many)
+constexpr int MAX_DEVICES = 64;
 
 struct TileInfo {
     int ty, tz;

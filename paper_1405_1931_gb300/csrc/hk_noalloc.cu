@@ -21,7 +21,7 @@ namespace {
 
 constexpr size_t SCRATCH_BYTES = (size_t)HK_NOALLOC_SCRATCH_BYTES;
 constexpr int TY = 16, TZ = 16;
-constexpr int MAX_DEVICES = 64;
+using hk::MAX_DEVICES;
 
 // Every GPU that loads the library holds this array until the process exits.
 __device__ __align__(256) unsigned char g_scratch[SCRATCH_BYTES];
