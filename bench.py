@@ -68,15 +68,15 @@ def dist_env():
 # number of sites.  It holds only for the kernel sources it was taken on, identified
 # by TRAFFIC_SOURCE_SHA; after any change to them it is reported as null.
 TRAFFIC_SITES = 512 ** 3
-TRAFFIC_BYTES = {"occupancy": 554.3e6, "tile_label": 63.6e6, "face_merge": 37.2e6, "piece_finalize": 30.0e6,
-                 "scan": 8.5e6, "lattice_finish": 0.0, "flatten": 629.3e6}
-TRAFFIC_SOURCE_SHA = "6fa90f53fdf7931a"
+TRAFFIC_BYTES = {"occupancy": 554.7e6, "tile_label": 63.8e6, "face_merge": 37.2e6, "piece_finalize": 30.0e6,
+                 "scan": 8.5e6, "lattice_finish": 0.0, "flatten": 629.5e6}
+TRAFFIC_SOURCE_SHA = "9a505727ee2baee0"
 # Warp instructions of one launch of the two instruction-bound passes at 512^3
 # (smsp__inst_executed.sum of one ncu capture; the summary with its command is
 # profiles/hk_label_kernels_critical512_full.md), scaled by sites like the traffic and
 # held to the same kernel sources.  Their roofline is the issue rate: 4 warp
 # schedulers per SM, each issuing at most one warp instruction per clock.
-INST_PER_LAUNCH = {"tile_label": 391974737, "flatten": 195871612}
+INST_PER_LAUNCH = {"tile_label": 391983299, "flatten": 195871612}
 
 
 def kernel_source_sha() -> str:
@@ -574,6 +574,30 @@ def main():
                "steps": k_e2e,
                "sync": {"value": job_gsites_per_s(world, N, ms_sync), "ms_per_step": ms_sync,
                         "entry": "hk_label_host, one step at a time"}}
+        # the host link this run had: 1 GiB pinned copies one way, and both ways at once
+        nb = min(N, 1 << 28)
+        h_in, d_in = phi_h.reshape(-1)[:nb], torch.empty(nb, dtype=torch.float32, device="cuda")
+        h_out, d_out = outs_h[0][0].reshape(-1)[:nb].view(torch.float32), phi.reshape(-1)[:nb]
+
+        def rate(fn, nbytes, reps=3):
+            fn()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                fn()
+            torch.cuda.synchronize()
+            return nbytes * reps / (time.perf_counter() - t0) / 1e9
+
+        def both():
+            with torch.cuda.stream(streams[0]):
+                d_in.copy_(h_in, non_blocking=True)
+            with torch.cuda.stream(streams[-1]):
+                h_out.copy_(d_out, non_blocking=True)
+
+        e2e["link_gbs"] = {"h2d": rate(lambda: d_in.copy_(h_in, non_blocking=True), 4 * nb),
+                           "d2h": rate(lambda: h_out.copy_(d_out, non_blocking=True), 4 * nb),
+                           "duplex_each_way": rate(both, 4 * nb)}
+        del d_in
         for m in more:
             m.close()
         del phi_h, outs_h
