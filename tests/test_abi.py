@@ -63,6 +63,15 @@ def test_host_argument_errors_need_no_gpu():
     assert lib.hk_label_batched(None, None, 1, None) == hk.HK_ERR_ARG
     assert lib.hk_set_tile(None, 16, 16) == hk.HK_ERR_ARG
     assert lib.hk_gen_iid(None, 4, 4, 4, 0, 0.5, None) == 1
+    # the later entry points check their arguments before any CUDA call too
+    assert lib.hk_label_host_async(None, None, 4, 4, 4, per, None, None, 0, None, None, None) == hk.HK_ERR_ARG
+    assert lib.hk_interior_state(None, None, 4, 4, 4, per, None, None) == hk.HK_ERR_ARG
+    assert lib.hk_interior_update(None, None, -1, None, None) == hk.HK_ERR_ARG
+    assert lib.hk_interior_update(None, None, 5, None, None) == hk.HK_ERR_ARG
+    assert lib.hk_interior_update(None, None, 0, None, None) == hk.HK_OK          # nothing to do
+    assert lib.hk_interior_update_sites(None, 10, None, None, -1, None) == hk.HK_ERR_ARG
+    assert lib.hk_interior_update_sites(None, 10, None, None, 3, None) == hk.HK_ERR_ARG
+    assert lib.hk_interior_update_sites(None, 10, None, None, 0, None) == hk.HK_OK
 
 
 def test_build_entry_compiles_everything():
