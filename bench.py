@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="headline config only")
     ap.add_argument("--served-requests", type=int, default=2000)
+    ap.add_argument("--capsule-state", action="store_true",
+                    help="only the interior state of moving capsules (Sec. 6) at --size, for profiling")
     return ap.parse_args()
 
 
@@ -416,11 +418,48 @@ def extra_configs(args, peak):
     return res
 
 
+def run_capsule_state(args):
+    """The interior state of moving capsules alone (Sec. 6): --steps full refreshes and
+    dense updates of an L^3 index field with 700 (L / 1024)^3 capsules, one JSON line."""
+    import torch
+    from paper_1405_1931_gb300 import fields, hk
+    L = args.size
+    shape = (L, L, L)
+    ncap = max(1, round(700 * (L / 1024) ** 3))
+    caps = fields.capsule_params(ncap, shape, seed=21, a_lo=8.0, a_hi=30.0)
+    index = torch.from_numpy(fields.capsule_index_field(shape, caps)).cuda()
+    lab = hk.Labeller(0)
+    state = torch.empty(shape, dtype=torch.int8, device="cuda")
+    upd = torch.empty_like(state)
+    for _ in range(max(args.warmup, 1)):
+        lab.interior_state(index, out=state)
+        hk.interior_update(state, index, out=upd)
+    torch.cuda.synchronize()
+    s0 = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record(s0)
+    for _ in range(args.steps):
+        lab.interior_state(index, out=state)
+    ev[1].record(s0)
+    for _ in range(args.steps):
+        hk.interior_update(state, index, out=upd)
+    ev[2].record(s0)
+    ev[2].synchronize()
+    assert torch.equal(upd, state)                 # a static field: the update changes nothing
+    print(json.dumps({"workload": f"{L}^3 index field, {len(caps)} capsules (semi-axes U[8,30]), periodic",
+                      "steps": args.steps, "refresh_ms": ev[0].elapsed_time(ev[1]) / args.steps,
+                      "update_dense_ms": ev[1].elapsed_time(ev[2]) / args.steps}), flush=True)
+    lab.close()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.capsule_state:
+        run_capsule_state(args)
         return
 
     import torch
