@@ -47,8 +47,9 @@ def parse():
     ap.add_argument("--size", type=int, default=L_HEADLINE, help="lattice side (default 1024)")
     ap.add_argument("--tile", default="", help="ty,tz tile override")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-streams", type=int, default=3,
-                    help="contexts (each on its own stream) that take alternate steps in the end-to-end run")
+    ap.add_argument("--e2e-streams", type=int, default=0,
+                    help="contexts (each on its own stream) that take alternate steps in the end-to-end run "
+                         "(default: 3 on one GPU, 2 per rank with several, to bound the pinned host memory)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="headline config only")
     ap.add_argument("--served-requests", type=int, default=2000)
@@ -564,11 +565,19 @@ def main():
         cap_h = 2 * n_clusters + 1024            # host sizes buffers: the count fits with room
         phi_h = torch.empty((L, L, L), dtype=torch.float32, pin_memory=True)
         phi_h.copy_(phi)
-        nstr = max(1, args.e2e_streams)
-        outs_h = [(torch.empty((L, L, L), dtype=torch.int32, pin_memory=True),
-                   torch.empty(cap_h, dtype=torch.int64, pin_memory=True),
-                   torch.empty(32, dtype=torch.int64, pin_memory=True),
-                   torch.empty(1, dtype=torch.int64, pin_memory=True)) for _ in range(nstr)]
+        nstr = args.e2e_streams if args.e2e_streams > 0 else (3 if world == 1 else 2)
+        outs_h = []
+        for _ in range(nstr):       # page-locked output sets; fewer contexts if the host runs short
+            try:
+                outs_h.append((torch.empty((L, L, L), dtype=torch.int32, pin_memory=True),
+                               torch.empty(cap_h, dtype=torch.int64, pin_memory=True),
+                               torch.empty(32, dtype=torch.int64, pin_memory=True),
+                               torch.empty(1, dtype=torch.int64, pin_memory=True)))
+            except RuntimeError:
+                if not outs_h:
+                    raise
+                break
+        nstr = len(outs_h)
         more = [hk.Labeller(local) for _ in range(nstr - 1)]
         for m in more:
             if args.tile:
