@@ -167,6 +167,23 @@ def cpu_baseline_oracle(side: int = 512, reps: int = 3):
             "sample": f"{reps} x {side}^3 iid phi at p=0.3116, periodic xyz (serial C oracle, {dt:.1f} s)"}
 
 
+def cpu_parallel_oracle(side: int = 512, reps: int = 3):
+    """The paper's parallel scheme (Sec. 3) on all host cores, one slab per thread, on the
+    same sample as the serial baseline; its result equals the serial oracle's."""
+    import oracle
+    from paper_1405_1931_gb300 import fields
+    oracle.load()
+    threads = os.cpu_count() or 1
+    phi = fields.iid_field(side, side, side, seed=0, occupancy=P_C)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.label_mt(phi, (1, 1, 1), threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": reps * side ** 3 / dt / 1e9, "unit": "Gsites/s", "cores": threads,
+            "kind": "the paper's parallel scheme (Sec. 3) on host threads",
+            "sample": f"{reps} x {side}^3 iid phi at p=0.3116, periodic xyz ({dt:.1f} s)"}
+
+
 def max_over_ranks(value: float, dist=None, device="cuda") -> float:
     """The maximum of a per-rank number over all ranks (the value itself for one process)."""
     if dist is None:
@@ -657,9 +674,17 @@ def main():
         torch.cuda.empty_cache()
         extra = extra_configs(args, peak)
 
-    cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    cpu = cpu_par = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_oracle()
+        # a report beside the baseline, run in a child process: never a reason for this run to fail
+        try:
+            res = subprocess.run([sys.executable, "-c", "import json, bench; print(json.dumps(bench.cpu_parallel_oracle()))"],
+                                 cwd=ROOT, capture_output=True, text=True, timeout=300)
+            cpu_par = json.loads(res.stdout.strip().splitlines()[-1]) if res.returncode == 0 else \
+                {"error": f"exit {res.returncode}: {res.stderr.strip()[-200:]}"}
+        except Exception as exc:
+            cpu_par = {"error": str(exc)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Gsites/s", "n_gpus": world, "steps": args.steps,
@@ -672,7 +697,7 @@ def main():
                 "n_clusters": n_clusters,
                 "passes_ms": dict(zip(names, passes)),
                 "roofline": roofline, "kernels": kernels, "configs": extra,
-                "cpu_baseline": cpu, "e2e": e2e,
+                "cpu_baseline": cpu, "cpu_parallel": cpu_par, "e2e": e2e,
                 "gpu_launches": LAUNCHES_PER_CALL * args.steps, "clocks": clk}
         print(json.dumps(line), flush=True)
     lab.close()

@@ -34,7 +34,8 @@ OK, ERR_ARG, ERR_TOO_LARGE, ERR_CAPACITY, ERR_NOMEM = 0, 1, 2, 3, 6
 
 def build(src: str = _SRC, out: str = _LIB, extra: tuple = ()) -> str:
     """Compile the oracle with gcc (portable flags only: it runs on x86 and Arm)."""
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-Wall", "-Wextra", *extra, "-o", out, src, "-lm"]
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-Wall", "-Wextra", *extra, "-o", out, src,
+           "-lm"]
     subprocess.run(cmd, check=True)
     return out
 
@@ -68,6 +69,10 @@ def _bind(lib):
     st = lib.hk_oracle_interior_state
     st.restype = ctypes.c_int
     st.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    mt = lib.hk_oracle_mt_label
+    mt.restype = ctypes.c_int
+    mt.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
     up = lib.hk_oracle_interior_update
     up.restype = ctypes.c_int
     up.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
@@ -127,6 +132,31 @@ def interior(index: np.ndarray, periodic=(1, 1, 1), sizes_cap: int | None = None
         raise RuntimeError(f"hk_oracle_interior failed with status {rc}")
     k = min(int(ncl[0]), int(sizes_cap))
     return labels, sizes[:k].copy(), hist, int(ncl[0]), inside[:k].copy()
+
+
+def label_mt(phi: np.ndarray, periodic=(1, 1, 1), threads: int = 0, sizes_cap: int | None = None, lib=None):
+    """The paper's parallel scheme (Sec. 3) on host threads, one slab of planes along z
+    per thread (``threads`` = 0: all host cores).  Same results as ``label``."""
+    lib = lib or load()
+    phi = np.ascontiguousarray(phi, dtype=np.float32)
+    if phi.ndim != 3:
+        raise ValueError("phi must have shape (nz, ny, nx)")
+    nz, ny, nx = phi.shape
+    n = phi.size
+    if sizes_cap is None:
+        sizes_cap = (n + 1) // 2
+    threads = threads or (os.cpu_count() or 1)
+    labels = np.empty(phi.shape, dtype=np.int32)
+    sizes = np.zeros(max(int(sizes_cap), 1), dtype=np.int64)
+    hist = np.zeros(32, dtype=np.int64)
+    ncl = np.zeros(1, dtype=np.int64)
+    per = np.array([int(bool(p)) for p in periodic], dtype=np.int32)
+    rc = lib.hk_oracle_mt_label(phi.ctypes.data, nx, ny, nz, per.ctypes.data, int(threads), labels.ctypes.data,
+                                sizes.ctypes.data, int(sizes_cap), hist.ctypes.data, ncl.ctypes.data)
+    if rc not in (OK, ERR_CAPACITY):
+        raise RuntimeError(f"hk_oracle_mt_label failed with status {rc}")
+    k = int(ncl[0])
+    return labels, sizes[:min(k, int(sizes_cap))].copy(), hist, k
 
 
 def interior_state(index: np.ndarray, periodic=(1, 1, 1), lib=None) -> np.ndarray:

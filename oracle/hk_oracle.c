@@ -80,6 +80,21 @@
  * a test checks this on capsules moving by under half a lattice constant per
  * step, and shows that it fails for a jump of several lattice constants.
  *
+ * hk_oracle_mt_label is the paper's parallel scheme (Sec. 3) on host threads, one
+ * thread for each process of a decomposition into slabs along z:
+ *   1. every domain is labelled by the serial algorithm above on its own sites,
+ *      its x and y periodic edges included;
+ *   2. n_max, the largest local label count, is shared, and local label k of
+ *      domain w becomes the global id w * n_max + k (Eq. 1);
+ *   3. halo: each domain reads the labels of the first plane of the next domain
+ *      along z (the last domain the first's, when z is periodic) and records an
+ *      equivalence of global ids for every pair of occupied sites across that face;
+ *   4. the equivalences are gathered at the root, which resolves them, gives every
+ *      class the smallest site index of its members and scatters that back;
+ *   5. every domain relabels its sites.
+ * The root computes the sizes, the compactified order and the histogram.  The
+ * result is the same as hk_oracle_label's (the output is unique); a test checks it.
+ *
  * hk_oracle_rc_histogram bins cluster sizes V by R_c, the radius of a sphere of
  * volume V (Fig. 5 caption: (4 pi / 3) R_c^3 = V), with caller-given ascending
  * edges e_0 < ... < e_{m-1}.  R_c >= e is decided as V >= t(e) with
@@ -88,7 +103,9 @@
  * e_{b-1} <= R_c < e_b and hist[m] counts R_c >= e_{m-1}.  rc_sum = sum of
  * cbrt(3 V / (4 pi)) over the clusters (for the mean droplet radius).
  */
+#define _POSIX_C_SOURCE 200809L   /* pthread barriers */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -111,6 +128,9 @@ int hk_oracle_rc_histogram(const int64_t *sizes, int64_t n, const double *edges,
 int hk_oracle_interior_state(const float *index, int nx, int ny, int nz, const int periodic[3],
                              int8_t *state_out);
 int hk_oracle_interior_update(const int8_t *state_prev, const float *index, int64_t n, int8_t *state_out);
+int hk_oracle_mt_label(const float *phi, int nx, int ny, int nz, const int periodic[3], int threads,
+                       int32_t *labels_out, int64_t *sizes_out, int64_t sizes_cap,
+                       int64_t *hist_out, int64_t *n_clusters_out);
 
 int hk_oracle_version(void) { return 1; }
 
@@ -372,4 +392,273 @@ int hk_oracle_interior_update(const int8_t *state_prev, const float *index, int6
     for (int64_t s = 0; s < n; ++s)
         state_out[s] = (index[s] < -0.5f) ? state_prev[s] : near_side(index[s]);
     return HKO_OK;
+}
+
+/* ---------------------------------------------------------------------------
+ * The parallel scheme of Sec. 3 on host threads (see the header).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int z0, z1;              /* the domain's planes */
+    label_table t;           /* its label-of-labels list and first sites (global indices) */
+    int32_t l_max;
+    int64_t *size;           /* [l_max + 1] sites of each local root */
+    int64_t *pairs;          /* equivalences across the face to the next domain, 2 global ids each */
+    int64_t npairs, cap;
+    int32_t *out;            /* [l_max + 1] final label of each local root (from the root) */
+    int rc;
+} mt_domain;
+
+typedef struct {
+    const float *phi;
+    int nx, ny, nz, P;
+    const int *periodic;
+    int32_t *l;
+    mt_domain *d;
+    pthread_barrier_t bar;
+    pthread_mutex_t gate_mu;   /* workers start once every thread exists (go), or leave (!ok) */
+    pthread_cond_t gate_cv;
+    int go, ok;
+    int64_t *sizes_out, sizes_cap, *hist_out, n;
+    int rc;
+} mt_job;
+
+typedef struct {
+    mt_job *job;
+    int w;
+} mt_arg;
+
+static int mt_push_pair(mt_domain *D, int64_t a, int64_t b) {
+    if (D->npairs == D->cap) {
+        int64_t nc = D->cap ? 2 * D->cap : 1024;
+        int64_t *np = (int64_t *)realloc(D->pairs, (size_t)nc * 2 * sizeof(int64_t));
+        if (!np) return HKO_ERR_NOMEM;
+        D->pairs = np;
+        D->cap = nc;
+    }
+    D->pairs[2 * D->npairs] = a;
+    D->pairs[2 * D->npairs + 1] = b;
+    D->npairs += 1;
+    return HKO_OK;
+}
+
+/* Step 1: the serial algorithm on the planes z0 .. z1 - 1; afterwards every
+ * occupied site holds its local root id and size[] counts the sites of each. */
+static int mt_local(mt_job *J, mt_domain *D) {
+    const int nx = J->nx, ny = J->ny;
+    const int64_t sx = 1, sy = nx, sz = (int64_t)nx * ny;
+    int32_t *l = J->l;
+    for (int64_t s = D->z0 * sz; s < D->z1 * sz; ++s) l[s] = (J->phi[s] > 0.0f) ? -1 : 0;
+    for (int z = D->z0; z < D->z1; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const int64_t s = x * sx + y * sy + z * sz;
+                if (l[s] != -1) continue;
+                int32_t nb[3];
+                int n_nb = 0;
+                if (x > 0 && l[s - sx] > 0) nb[n_nb++] = l[s - sx];
+                if (y > 0 && l[s - sy] > 0) nb[n_nb++] = l[s - sy];
+                if (z > D->z0 && l[s - sz] > 0) nb[n_nb++] = l[s - sz];   /* not across the domain face */
+                if (n_nb == 0) {
+                    D->l_max += 1;
+                    if (table_push(&D->t, D->l_max, s) != HKO_OK) return HKO_ERR_NOMEM;
+                    l[s] = D->l_max;
+                } else {
+                    int32_t m = nb[0];
+                    for (int i = 1; i < n_nb; ++i) if (nb[i] < m) m = nb[i];
+                    l[s] = m;
+                    for (int i = 0; i < n_nb; ++i)
+                        for (int j = i + 1; j < n_nb; ++j) store_equivalence(D->t.lol, nb[i], nb[j]);
+                }
+            }
+    /* the periodic edges inside the domain: x and y always, z when one domain holds all planes */
+    for (int z = D->z0; z < D->z1; ++z) {
+        if (J->periodic[0] && nx >= 2)
+            for (int y = 0; y < ny; ++y) {
+                const int64_t a = (nx - 1) * sx + y * sy + z * sz, b = y * sy + z * sz;
+                if (l[a] > 0 && l[b] > 0) store_equivalence(D->t.lol, l[a], l[b]);
+            }
+        if (J->periodic[1] && ny >= 2)
+            for (int x = 0; x < nx; ++x) {
+                const int64_t a = x * sx + (ny - 1) * sy + z * sz, b = x * sx + z * sz;
+                if (l[a] > 0 && l[b] > 0) store_equivalence(D->t.lol, l[a], l[b]);
+            }
+    }
+    if (J->P == 1 && J->periodic[2] && J->nz >= 2)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const int64_t a = x * sx + y * sy + (J->nz - 1) * sz, b = x * sx + y * sy;
+                if (l[a] > 0 && l[b] > 0) store_equivalence(D->t.lol, l[a], l[b]);
+            }
+    D->size = (int64_t *)calloc((size_t)D->l_max + 1, sizeof(int64_t));
+    if (!D->size) return HKO_ERR_NOMEM;
+    for (int32_t k = 1; k <= D->l_max; ++k) D->t.lol[k] = list_end(D->t.lol, k);
+    for (int64_t s = D->z0 * sz; s < D->z1 * sz; ++s)
+        if (l[s] > 0) {
+            l[s] = D->t.lol[l[s]];
+            D->size[l[s]] += 1;
+        }
+    return HKO_OK;
+}
+
+static int64_t mt_find(int64_t *parent, int64_t x) {
+    while (parent[x] != x) {
+        parent[x] = parent[parent[x]];
+        x = parent[x];
+    }
+    return x;
+}
+
+/* Step 4 at the root: resolve the gathered equivalences over all local roots. */
+static int mt_resolve(mt_job *J, int64_t n_max) {
+    const int P = J->P;
+    int64_t *off = (int64_t *)malloc((size_t)(P + 1) * sizeof(int64_t));
+    if (!off) return HKO_ERR_NOMEM;
+    off[0] = 0;
+    for (int w = 0; w < P; ++w) off[w + 1] = off[w] + J->d[w].l_max;
+    const int64_t T = off[P];
+    int64_t *parent = (int64_t *)malloc((size_t)(T > 0 ? T : 1) * sizeof(int64_t));
+    int64_t *minsite = (int64_t *)malloc((size_t)(T > 0 ? T : 1) * sizeof(int64_t));
+    int64_t *csize = (int64_t *)calloc((size_t)(T > 0 ? T : 1), sizeof(int64_t));
+    int rc = (parent && minsite && csize) ? HKO_OK : HKO_ERR_NOMEM;
+    if (rc == HKO_OK) {
+        for (int64_t i = 0; i < T; ++i) { parent[i] = i; minsite[i] = INT64_MAX; }
+        /* a global id g = w * n_max + k (Eq. 1) is local root k of domain w */
+        for (int w = 0; w < P; ++w)
+            for (int64_t e = 0; e < J->d[w].npairs; ++e) {
+                const int64_t ga = J->d[w].pairs[2 * e], gb = J->d[w].pairs[2 * e + 1];
+                const int64_t wa = (ga - 1) / n_max, wb = (gb - 1) / n_max;
+                const int64_t a = mt_find(parent, off[wa] + (ga - wa * n_max) - 1);
+                const int64_t b = mt_find(parent, off[wb] + (gb - wb * n_max) - 1);
+                if (a < b) parent[b] = a;
+                else if (b < a) parent[a] = b;
+            }
+        for (int w = 0; w < P; ++w)
+            for (int32_t k = 1; k <= J->d[w].l_max; ++k) {
+                if (J->d[w].size[k] == 0) continue;                 /* not a local root */
+                const int64_t r = mt_find(parent, off[w] + k - 1);
+                if (J->d[w].t.first[k] < minsite[r]) minsite[r] = J->d[w].t.first[k];
+                csize[r] += J->d[w].size[k];
+            }
+        /* compactified order: domains in z order and each domain's local roots in
+         * creation (raster) order visit first sites in increasing order; a class is
+         * counted at the local root that holds its smallest site */
+        int64_t n = 0;
+        for (int b = 0; b < 32; ++b) J->hist_out[b] = 0;
+        for (int w = 0; w < P; ++w)
+            for (int32_t k = 1; k <= J->d[w].l_max; ++k) {
+                if (J->d[w].size[k] == 0) continue;
+                const int64_t r = mt_find(parent, off[w] + k - 1);
+                if (minsite[r] != J->d[w].t.first[k]) continue;
+                int b = 0;
+                while (((int64_t)2 << b) <= csize[r]) ++b;
+                J->hist_out[b] += 1;
+                if (n < J->sizes_cap) J->sizes_out[n] = csize[r];
+                ++n;
+            }
+        J->n = n;
+        /* scatter: the final label of every local root */
+        for (int w = 0; w < P && rc == HKO_OK; ++w) {
+            mt_domain *D = &J->d[w];
+            D->out = (int32_t *)malloc((size_t)(D->l_max + 1) * sizeof(int32_t));
+            if (!D->out) { rc = HKO_ERR_NOMEM; break; }
+            for (int32_t k = 1; k <= D->l_max; ++k)
+                D->out[k] = D->size[k] ? (int32_t)minsite[mt_find(parent, off[w] + k - 1)] : -1;
+        }
+    }
+    free(off); free(parent); free(minsite); free(csize);
+    return rc;
+}
+
+static void *mt_worker(void *p) {
+    mt_arg *a = (mt_arg *)p;
+    mt_job *J = a->job;
+    const int w = a->w;
+    mt_domain *D = &J->d[w];
+    const int64_t sy = J->nx, sz = (int64_t)J->nx * J->ny;
+    pthread_mutex_lock(&J->gate_mu);
+    while (!J->go) pthread_cond_wait(&J->gate_cv, &J->gate_mu);
+    const int ok = J->ok;
+    pthread_mutex_unlock(&J->gate_mu);
+    if (!ok) return NULL;
+    D->rc = mt_local(J, D);
+    pthread_barrier_wait(&J->bar);
+    /* steps 2-3: Eq. 1's offsets and the equivalences across the face to the next domain */
+    int64_t n_max = 1;
+    for (int v = 0; v < J->P; ++v) if (J->d[v].l_max > n_max) n_max = J->d[v].l_max;
+    const int next = (w + 1 < J->P) ? w + 1 : ((J->periodic[2] && J->nz >= 2 && J->P >= 2) ? 0 : -1);
+    if (D->rc == HKO_OK && next >= 0) {
+        const int zt = D->z1 - 1, zb = J->d[next].z0;
+        for (int y = 0; y < J->ny && D->rc == HKO_OK; ++y)
+            for (int x = 0; x < J->nx; ++x) {
+                const int32_t la = J->l[x + y * sy + zt * sz], lb = J->l[x + y * sy + zb * sz];
+                if (la > 0 && lb > 0) {
+                    D->rc = mt_push_pair(D, w * n_max + la, next * n_max + lb);
+                    if (D->rc != HKO_OK) break;
+                }
+            }
+    }
+    pthread_barrier_wait(&J->bar);
+    if (w == 0) {                                          /* step 4: gather at the root */
+        J->rc = HKO_OK;
+        for (int v = 0; v < J->P; ++v) if (J->d[v].rc != HKO_OK) J->rc = J->d[v].rc;
+        if (J->rc == HKO_OK) J->rc = mt_resolve(J, n_max);
+    }
+    pthread_barrier_wait(&J->bar);
+    if (J->rc == HKO_OK)                                   /* step 5: relabel */
+        for (int64_t s = D->z0 * sz; s < D->z1 * sz; ++s) J->l[s] = J->l[s] > 0 ? D->out[J->l[s]] : -1;
+    return NULL;
+}
+
+int hk_oracle_mt_label(const float *phi, int nx, int ny, int nz, const int periodic[3], int threads,
+                       int32_t *labels_out, int64_t *sizes_out, int64_t sizes_cap,
+                       int64_t *hist_out, int64_t *n_clusters_out) {
+    if (!phi || !periodic || !labels_out || !hist_out || !n_clusters_out || threads < 1) return HKO_ERR_ARG;
+    if (nx < 1 || ny < 1 || nz < 1 || sizes_cap < 0) return HKO_ERR_ARG;
+    if (sizes_cap > 0 && !sizes_out) return HKO_ERR_ARG;
+    if ((int64_t)nx * ny * nz >= ((int64_t)1 << 31)) return HKO_ERR_TOO_LARGE;
+    const int P = threads < nz ? threads : nz;
+    mt_job J;
+    memset(&J, 0, sizeof(J));
+    J.phi = phi; J.nx = nx; J.ny = ny; J.nz = nz; J.P = P; J.periodic = periodic; J.l = labels_out;
+    J.sizes_out = sizes_out; J.sizes_cap = sizes_cap; J.hist_out = hist_out;
+    J.d = (mt_domain *)calloc((size_t)P, sizeof(mt_domain));
+    pthread_t *th = (pthread_t *)malloc((size_t)P * sizeof(pthread_t));
+    mt_arg *args = (mt_arg *)malloc((size_t)P * sizeof(mt_arg));
+    if (!J.d || !th || !args || pthread_barrier_init(&J.bar, NULL, (unsigned)P) != 0) {
+        free(J.d); free(th); free(args);
+        return HKO_ERR_NOMEM;
+    }
+    pthread_mutex_init(&J.gate_mu, NULL);
+    pthread_cond_init(&J.gate_cv, NULL);
+    for (int w = 0; w < P; ++w) {
+        J.d[w].z0 = (int)((int64_t)w * nz / P);
+        J.d[w].z1 = (int)((int64_t)(w + 1) * nz / P);
+        args[w].job = &J;
+        args[w].w = w;
+    }
+    int started = 1;
+    while (started < P && pthread_create(&th[started], NULL, mt_worker, &args[started]) == 0) ++started;
+    /* open the gate: with every thread running they all take part; otherwise the ones
+     * that started leave before any barrier */
+    pthread_mutex_lock(&J.gate_mu);
+    J.go = 1;
+    J.ok = started == P;
+    pthread_cond_broadcast(&J.gate_cv);
+    pthread_mutex_unlock(&J.gate_mu);
+    int rc = HKO_ERR_NOMEM;
+    if (J.ok) {
+        mt_worker(&args[0]);
+        rc = J.rc;
+    }
+    for (int w = 1; w < started; ++w) pthread_join(th[w], NULL);
+    pthread_cond_destroy(&J.gate_cv);
+    pthread_mutex_destroy(&J.gate_mu);
+    if (rc == HKO_OK) *n_clusters_out = J.n;
+    pthread_barrier_destroy(&J.bar);
+    for (int w = 0; w < P; ++w) {
+        free(J.d[w].t.lol); free(J.d[w].t.first); free(J.d[w].size); free(J.d[w].pairs); free(J.d[w].out);
+    }
+    free(J.d); free(th); free(args);
+    if (rc != HKO_OK) return rc;
+    return J.n > sizes_cap ? HKO_ERR_CAPACITY : HKO_OK;
 }

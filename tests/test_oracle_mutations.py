@@ -21,23 +21,26 @@ SRC = os.path.join(os.path.dirname(oracle.__file__), "hk_oracle.c")
 
 MUTATIONS = {
     "drop_z_neighbour": ("if (z > 0 && l[s - sz] > 0) nb[n_nb++] = l[s - sz];", ""),
-    "drop_y_neighbour": ("if (y > 0 && l[s - sy] > 0) nb[n_nb++] = l[s - sy];", ""),
+    "drop_y_neighbour": ("if (y > 0 && l[s - sy] > 0) nb[n_nb++] = l[s - sy];\n                if (z > 0 &&",
+                         "if (z > 0 &&"),
     # (taking the max instead of the min in rule 3 is an equivalent mutant: the final
     # relabelling reduces every id to its class minimum, so it is not listed)
-    "rule3_first_pair_only": ("for (int j = i + 1; j < n_nb; ++j)", "for (int j = i + 1; j < 2; ++j)"),
+    "rule3_first_pair_only": ("for (int j = i + 1; j < n_nb; ++j)\n                            store_equivalence(t.lol",
+                              "for (int j = i + 1; j < 2; ++j)\n                            store_equivalence(t.lol"),
     "rule3_no_equivalence": ("store_equivalence(t.lol, nb[i], nb[j]);", "(void)j;"),
     "link_larger_end_wrong_way": ("if (ea < eb) lol[eb] = ea;", "if (ea < eb) lol[ea] = eb;"),
     "occupancy_ge": ("(phi[s] > 0.0f) ? -1 : 0", "(phi[s] >= 0.0f) ? -1 : 0"),
     "drop_x_wrap": ("if (periodic[0] && nx >= 2)", "if (0)"),
     "drop_z_wrap": ("if (periodic[2] && nz >= 2)", "if (0)"),
-    "wrap_off_by_one": ("int64_t a = x * sx + (ny - 1) * sy + z * sz", "int64_t a = x * sx + (ny - 2) * sy + z * sz"),
+    "wrap_off_by_one": ("                int64_t a = x * sx + (ny - 1) * sy + z * sz",
+                        "                int64_t a = x * sx + (ny - 2) * sy + z * sz"),
     "wrap_axis_swapped": ("if (periodic[1] && ny >= 2)", "if (periodic[0] && ny >= 2)"),
     "hist_off_by_one": ("while (((int64_t)2 << b) <= size) ++b;", "while (((int64_t)1 << b) <= size) ++b;"),
     "label_is_compact_id": ("l[s] = (int32_t)t.first[root];", "l[s] = compact[root];"),
     "sizes_shifted": ("if (c - 1 < sizes_cap) sizes_out[c - 1] = size;",
                       "if (c - 1 < sizes_cap) sizes_out[(c % n)] = size;"),
-    "raster_y_stride": ("const int64_t sx = 1, sy = nx, sz = (int64_t)nx * ny;",
-                        "const int64_t sx = 1, sy = ny, sz = (int64_t)nx * ny;"),
+    "raster_y_stride": ("const int64_t sx = 1, sy = nx, sz = (int64_t)nx * ny;\n    const int64_t N =",
+                        "const int64_t sx = 1, sy = ny, sz = (int64_t)nx * ny;\n    const int64_t N ="),
     # interior/exterior identification (Sec. 6, steps 3-5)
     "interior_vote_sign": ("const int sign = (v < 0.0f) ? -1 : (v > 0.0f) ? 1 : 0;",
                            "const int sign = (v < 0.0f) ? 1 : (v > 0.0f) ? -1 : 0;"),
