@@ -680,7 +680,7 @@ def main():
         # a report beside the baseline, run in a child process: never a reason for this run to fail
         try:
             res = subprocess.run([sys.executable, "-c", "import json, bench; print(json.dumps(bench.cpu_parallel_oracle()))"],
-                                 cwd=ROOT, capture_output=True, text=True, timeout=300)
+                                 cwd=ROOT, capture_output=True, text=True, timeout=120)
             cpu_par = json.loads(res.stdout.strip().splitlines()[-1]) if res.returncode == 0 else \
                 {"error": f"exit {res.returncode}: {res.stderr.strip()[-200:]}"}
         except Exception as exc:
