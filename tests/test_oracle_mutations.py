@@ -57,6 +57,11 @@ MUTATIONS = {
                                 "state_out[s] = state_prev[s];"),
     "update_far_le": ("state_out[s] = (index[s] < -0.5f) ? state_prev[s] : near_side(index[s]);",
                       "state_out[s] = (index[s] <= -0.5f) ? state_prev[s] : near_side(index[s]);"),
+    # the paper's parallel scheme on host threads (Sec. 3)
+    "mt_drop_halo": ("if (la > 0 && lb > 0) {", "if (0) {"),
+    "mt_no_z_wrap": ("((J->periodic[2] && J->nz >= 2 && J->P >= 2) ? 0 : -1)", "(-1)"),
+    "mt_offset_collides": ("D->rc = mt_push_pair(D, w * n_max + la, next * n_max + lb);",
+                           "D->rc = mt_push_pair(D, la, lb);"),
     # droplet-size histogram by R_c (Fig. 5)
     "rc_bin_shift": ("if (V >= ((e * e) * e) * four_thirds_pi) bin = b + 1;", "if (V >= ((e * e) * e) * four_thirds_pi) bin = b;"),
     "rc_radius_not_cubed": ("if (V >= ((e * e) * e) * four_thirds_pi) bin = b + 1;",
@@ -119,6 +124,13 @@ def battery(lib):
     st = np.array([1, 0, -1, 1, 0, 1, 0, 0], dtype=np.int8).reshape(1, 1, 8)
     ix = np.array([-1.0, -1.0, -1.0, 0.25, -0.25, 0.0, np.nan, -0.5], dtype=np.float32).reshape(1, 1, 8)
     assert oracle.interior_update(st, ix, lib=lib).reshape(-1).tolist() == [1, 0, -1, 0, 1, 0, 0, 1]
+    # the parallel scheme against the brute force, over slabs of one to several planes
+    for it in range(30):
+        shape = tuple(int(v) for v in rng.integers(1, 7, size=3))
+        occ = rng.random(shape) < rng.uniform(0.3, 0.7)
+        per = pers[it % 8]
+        same(oracle.label_mt(np.where(occ, 1.0, -1.0).astype(np.float32), per, threads=3, lib=lib),
+             bfs_label(occ, per))
     # droplet-size histogram by R_c: hand-worked example
     h, rc_sum = oracle.rc_histogram([1, 8, 27, 1000], [0.5, 1.0, 2.0, 5.0, 10.0], lib=lib)
     assert h.tolist() == [0, 1, 2, 0, 1, 0]
