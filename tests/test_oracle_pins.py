@@ -321,3 +321,23 @@ def test_capacity_and_arguments():
     assert n == 32 and sizes.size == 10 and hist.sum() == 32
     assert oracle.status(phi, (0, 0, 0), sizes_cap=10) == oracle.ERR_CAPACITY
     assert oracle.status(phi, (0, 0, 0), sizes_cap=32) == oracle.OK
+
+
+def test_singleton_fraction_at_p_c():
+    """Statistical sanity (not parity): on a periodic i.i.d. lattice a site is a one-site
+    cluster iff it is occupied and its six neighbours are empty, so the expected number of
+    size-1 clusters per site is p (1 - p)^6 (0.0332 at p = 0.3116).  64^3 sites: within 4 %."""
+    from paper_1405_1931_gb300 import fields
+    p = 0.3116
+    phi = fields.iid_field(64, 64, 64, seed=4, occupancy=p)
+    labels, sizes, hist, n = oracle.label(phi, (1, 1, 1))
+    occ = phi > 0
+    assert hist[0] == int((sizes == 1).sum())
+    per_site = hist[0] / phi.size
+    assert abs(per_site - p * (1 - p) ** 6) < 0.04 * p * (1 - p) ** 6
+    # and directly from the definition on the same lattice
+    empty_nbrs = np.ones_like(occ)
+    for axis in range(3):
+        for d in (-1, 1):
+            empty_nbrs &= ~np.roll(occ, d, axis=axis)
+    assert hist[0] == int((occ & empty_nbrs).sum())
