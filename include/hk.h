@@ -113,8 +113,9 @@ int hk_label(hk_ctx *ctx, const float *phi, int nx, int ny, int nz, const int pe
  * votes with the sign of I at the near site (I == 0 and NaN do not vote); more
  * negative votes -> interior, more positive -> exterior, a tie -> -1.
  * Same stream and capacity rules as hk_label; the tags of clusters beyond
- * sizes_cap are not written.  The workspace grows by 4 B per site/8 and 4 B per
- * sizes_cap entry for the votes.
+ * sizes_cap are not written.  The workspace grows by N/4 bytes (a word of root
+ * sites and a rank prefix per 32-site row segment) and 4 B per sizes_cap entry
+ * for the votes.
  * Errors: HK_ERR_ARG, HK_ERR_TOO_LARGE, HK_ERR_NOMEM, HK_ERR_CUDA, HK_ERR_CAPACITY. */
 int hk_label_interior(hk_ctx *ctx, const float *index, int nx, int ny, int nz, const int periodic[3],
                       int32_t *labels_out, int64_t *sizes_out, int64_t sizes_cap,
