@@ -78,3 +78,21 @@ def test_build_entry_compiles_everything():
     import __graft_entry__ as g
     g.build()
     assert os.path.exists(hk.lib_path())
+
+
+def test_headers_are_plain_c_and_link(tmp_path):
+    """The boundary is a C ABI: a C99 program that includes both headers and takes the
+    address of every declared entry point compiles with gcc and links against libhk.so."""
+    lib = hk.load()
+    names = declared_symbols()
+    src = tmp_path / "use_abi.c"
+    src.write_text('#include "hk.h"\n#include "hk_gen.h"\n#include <stdio.h>\n'
+                   "int main(void) {\n    const void *entries[] = {\n"
+                   + "".join(f"        (const void *)&{n},\n" for n in names)
+                   + "    };\n    printf(\"%d\\n\", (int)(sizeof entries / sizeof entries[0]));\n"
+                   "    return 0;\n}\n")
+    exe = tmp_path / "use_abi"
+    libdir = os.path.dirname(lib._name)
+    import subprocess
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-o", str(exe), "-L", libdir, "-lhk", f"-Wl,-rpath,{libdir}"], check=True)
