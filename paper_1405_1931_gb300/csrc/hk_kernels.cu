@@ -148,8 +148,13 @@ __global__ void __launch_bounds__(256) k_occupancy_tma(const __grid_constant__ T
     int k = 0;
     for (int64_t t = t0; t < ntiles; t += step, ++k) {
         const int s = k & 1;
-        if (!mbar_wait_bounded(&S.bar[s], (uint32_t)((k >> 1) & 1))) {
+        // the decision to give up is the CTA's, so that every thread leaves together
+        if (__syncthreads_or(!mbar_wait_bounded(&S.bar[s], (uint32_t)((k >> 1) & 1)))) {
             if (tid == 0) atomicOr(W.status, STATUS_TMA_TIMEOUT);
+            // a second bounded wait for the copies still in flight into this CTA's
+            // buffers (this tile's and the next one's) before its shared memory goes
+            mbar_wait_bounded(&S.bar[s], (uint32_t)((k >> 1) & 1));
+            if (t + step < ntiles) mbar_wait_bounded(&S.bar[s ^ 1], (uint32_t)(((k + 1) >> 1) & 1));
             return;
         }
         const LatDev &L = B.lat[(NL == 1) ? 0 : find_lattice(B.lat, B.n, t)];
