@@ -66,3 +66,27 @@ def test_capacity_and_arguments():
     n = np.zeros(1, dtype=np.int64)
     assert lib.hk_oracle_mt_label(phi.ctypes.data, 20, 20, 20, per.ctypes.data, 0, out.ctypes.data, None, 0,
                                   hist.ctypes.data, n.ctypes.data) == oracle.ERR_ARG
+
+
+def test_two_process_wrap_merge():
+    """The situation of Fig. 2 (whose lattice is not reproducible): two processes on a
+    periodic lattice whose local clusters are joined only through the face between them,
+    the periodic z edge and the x wrap, leaving two clusters.  Lattice (z rows, x columns,
+    ny = 1), slabs z = 0-1 and z = 2-3:
+        z=0: X . X . . X
+        z=1: X . . . . .
+        z=2: X . . . X .
+        z=3: . . X . X X
+    Process 0 has local clusters {x=0 column, x=5 via the x wrap} and {(2,0)}; process 1
+    has three.  The face z=1|z=2 and the z wrap join them into {7 sites, first site 0} and
+    {(2,0), (2,3)}; without periodic edges there are five clusters."""
+    rows = ["X.X..X", "X.....", "X...X.", "..X.XX"]
+    occ = np.array([[c == "X" for c in r] for r in rows]).reshape(4, 1, 6)
+    phi = np.where(occ, 1.0, -1.0).astype(np.float32)
+    for got in (oracle.label(phi, (1, 1, 1)), oracle.label_mt(phi, (1, 1, 1), threads=2)):
+        assert got[3] == 2
+        assert got[1].tolist() == [7, 2]
+        lab = got[0].reshape(4, 6)
+        assert set(lab[occ.reshape(4, 6)].tolist()) == {0, 2}
+        assert lab[0, 2] == 2 and lab[3, 2] == 2 and lab[3, 5] == 0
+    assert oracle.label_mt(phi, (0, 0, 0), threads=2)[3] == 5

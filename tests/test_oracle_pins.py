@@ -341,3 +341,18 @@ def test_singleton_fraction_at_p_c():
         for d in (-1, 1):
             empty_nbrs &= ~np.roll(occ, d, axis=axis)
     assert hist[0] == int((occ & empty_nbrs).sum())
+
+
+def test_gyroid_labyrinths_are_one_cluster_each():
+    """A bijel is one cluster (Sec. 5).  The stand-in is the gyroid
+    sin x cos y + sin y cos z + sin z cos x over one period: each of its two interpenetrating
+    labyrinths is connected, so phi > 0 and phi < 0 are one cluster each, with and without
+    periodic edges."""
+    for L in (24, 32):
+        t = 2 * np.pi * np.arange(L) / L
+        z, y, x = np.meshgrid(t, t, t, indexing="ij")
+        phi = (np.sin(x) * np.cos(y) + np.sin(y) * np.cos(z) + np.sin(z) * np.cos(x)).astype(np.float32)
+        for per in [(1, 1, 1), (0, 0, 0)]:
+            for f in (phi, -phi):
+                labels, sizes, hist, n = oracle.label(f, per)
+                assert n == 1 and sizes[0] == int((f > 0).sum())
