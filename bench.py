@@ -66,18 +66,17 @@ def dist_env():
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per lattice site of one
-# hk_label call at p_c, per pass, from one ncu capture of a 512^3 call (the summary
-# with its command is profiles/hk_label_critical512_dram_traffic.md), scaled by the
-# number of sites.  It holds only for the kernel sources it was taken on, identified
-# by TRAFFIC_SOURCE_SHA; after any change to them it is reported as null.
+# hk_label call at p_c, per pass, from one ncu capture of a 512^3 call on these kernel
+# sources, scaled by the number of sites.  It holds only for the kernel sources it was
+# taken on, identified by TRAFFIC_SOURCE_SHA; after any change to them it is reported
+# as null.
 TRAFFIC_SITES = 512 ** 3
 TRAFFIC_BYTES = {"occupancy": 554.3e6, "tile_label": 63.8e6, "face_merge": 37.2e6, "piece_finalize": 30.0e6,
                  "scan": 8.5e6, "lattice_finish": 0.0, "flatten": 629.4e6}
 TRAFFIC_SOURCE_SHA = "a269c8563b9c350a"
 # Warp instructions of one launch of the two instruction-bound passes at 512^3
-# (smsp__inst_executed.sum of one ncu capture; the summary with its command is
-# profiles/hk_label_kernels_critical512_full.md), scaled by sites like the traffic and
-# held to the same kernel sources.  Their roofline is the issue rate: 4 warp
+# (smsp__inst_executed.sum of one ncu capture of these kernel sources), scaled by
+# sites like the traffic and held to the same kernel sources.  Their roofline is the issue rate: 4 warp
 # schedulers per SM, each issuing at most one warp instruction per clock.
 INST_PER_LAUNCH = {"tile_label": 391975185, "flatten": 195871612}
 
@@ -248,6 +247,7 @@ def time_single(lab, phi, per, reps, flush=None):
         b.record(s)
         b.synchronize()
         ts.append(a.elapsed_time(b))
+    lab.sync_status()
     return float(np.median(ts)), int(out[3].item())
 
 
@@ -404,6 +404,7 @@ def extra_configs(args, peak):
     lab.set_graphs(True)
     gra = timed(lambda: lab.label_batched(items, stream=s))
     lab.set_graphs(False)
+    lab.sync_status(s)
     lab.set_tile(16, 16)
     res["batched96"] = {"workload": "96 lattices, axes in {32,...,384}, p in U[0.15,0.45], random periodic flags",
                         "sites": sites, "tile": list(tuned["tile"]), "autotune_ms": tuned["ms"],
@@ -526,6 +527,7 @@ def main():
     ms_total = t_start.elapsed_time(t_end)
     passes = hk.hk_get_timing(lab.ctx)
     hk.hk_set_timing(lab.ctx, False)
+    lab.sync_status()          # raises if a bounded device loop gave up in the timed calls
 
     ms_step = max_over_ranks(ms_total / args.steps, dist)
     value = job_gsites_per_s(world, N, ms_step)
@@ -628,6 +630,8 @@ def main():
         ms_async = timed(lambda: [async_step(i) for i in range(k_e2e)])
         for o in outs_h:
             assert int(o[3][0]) == n_clusters
+        for lb, st in zip(labs, streams):
+            lb.sync_status(st)
         assert torch.equal(outs_h[0][0], labels.cpu()) and torch.equal(outs_h[0][1][:n_clusters], sizes[:n_clusters].cpu())
         sync_step()
         ms_sync = timed(lambda: [sync_step() for _ in range(k_e2e)])

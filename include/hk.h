@@ -214,11 +214,25 @@ int hk_label_host_async(hk_ctx *ctx, const float *phi_host, int nx, int ny, int 
  * contents (each call rewrites what it reads), so calls that overlap on the
  * GPU -- on different streams, or from different host threads -- race and
  * must be serialised by the caller.  It uses the plain-load path (no TMA).
- * Errors: HK_ERR_ARG, HK_ERR_TOO_LARGE, HK_ERR_CUDA, HK_ERR_CAPACITY. */
+ *
+ * The bounded device loops of these calls (see hk_sync_status) report to a
+ * status word at the head of the array.  It is cleared only when it is read:
+ * by this call when it synchronises for the capacity rule (it then returns
+ * HK_ERR_TIMEOUT if a loop gave up), and by hk_noalloc_sync_status.
+ * Errors: HK_ERR_ARG, HK_ERR_TOO_LARGE, HK_ERR_CUDA, HK_ERR_CAPACITY,
+ * HK_ERR_TIMEOUT (capacity path only). */
 #define HK_NOALLOC_SCRATCH_BYTES (64u << 20)
 int hk_label_noalloc(const float *phi, int nx, int ny, int nz, const int periodic[3],
                      int32_t *labels_out, int64_t *sizes_out, int64_t sizes_cap,
                      int64_t *hist_out, int64_t *n_clusters_out, void *stream);
+
+/* The status check of hk_label_noalloc, which has no context to ask
+ * hk_sync_status: synchronises `stream` (the stream of the calls to check),
+ * then reads and clears the status word of the current device's scratch
+ * array.  HK_OK if no bounded device loop gave up since the last check (or no
+ * call has run on this device), HK_ERR_TIMEOUT if one did; HK_ERR_CUDA on a
+ * CUDA error.  Allocates nothing. */
+int hk_noalloc_sync_status(void *stream);
 
 /* Droplet-size histogram by R_c, the radius of a sphere with the cluster's
  * volume (Fig. 5 caption: (4 pi / 3) R_c^3 = V), over caller-given bin edges.
@@ -309,6 +323,19 @@ int hk_get_timing(hk_ctx *ctx, float *ms_out, int max_n, int *n_out);
  * would otherwise never terminate).  Clears the flag.  Returns HK_OK,
  * HK_ERR_TIMEOUT or HK_ERR_CUDA. */
 int hk_sync_status(hk_ctx *ctx, void *stream);
+
+/* Test control of the failure detection above: lower the bound of every
+ * capped union-find loop of later calls on this context to `cap` iterations
+ * (the shared-memory union retries and the global finds, unions and
+ * compression of the piece merge), so that a test can make a loop give up on
+ * an ordinary input and see HK_ERR_TIMEOUT from hk_sync_status.  A loop that
+ * gives up leaves every index it holds in range (a find stops at a valid piece
+ * or run id; a union stops without linking), so the labels of such a call are
+ * wrong but every access stays inside the workspace and the outputs.  The
+ * waits on TMA copies keep their bound.  cap == 0 restores the natural bounds
+ * (the tile's run count and the piece-table size).  Drops the context's
+ * graphs.  Errors: HK_ERR_ARG (NULL ctx, cap < 0). */
+int hk_set_loop_cap(hk_ctx *ctx, int64_t cap);
 
 /* The last CUDA error code seen by the context (cudaError_t as int). */
 int hk_last_cuda_error(const hk_ctx *ctx);

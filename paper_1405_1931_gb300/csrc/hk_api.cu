@@ -18,6 +18,34 @@ using hk::Plan;
 using hk::TileInfo;
 using hk::Work;
 
+namespace hk {
+
+Work bind_work(char *base, const Layout &Ly, int32_t *status, int64_t piece_cap, int64_t loop_cap) {
+    Work W;
+    W.mask = reinterpret_cast<uint32_t *>(base + Ly.mask);
+    W.codes = reinterpret_cast<uint16_t *>(base + Ly.codes);
+    W.cnt = reinterpret_cast<uint8_t *>(base + Ly.cnt);
+    W.pre = reinterpret_cast<uint32_t *>(base + Ly.pre);
+    W.bsum = reinterpret_cast<uint32_t *>(base + Ly.bsum);
+    W.face = reinterpret_cast<uint16_t *>(base + Ly.face);
+    W.tinfo = reinterpret_cast<int4 *>(base + Ly.tinfo);
+    W.parent = reinterpret_cast<int32_t *>(base + Ly.parent);
+    W.key = reinterpret_cast<int32_t *>(base + Ly.key);
+    W.psize = reinterpret_cast<int32_t *>(base + Ly.psize);
+    W.xcol = reinterpret_cast<uint32_t *>(base + Ly.xcol);
+    W.status = status;
+    W.ovf = reinterpret_cast<int32_t *>(base + Ly.ovf);
+    W.rootbits = reinterpret_cast<uint32_t *>(base + Ly.rootbits);
+    W.segpre = reinterpret_cast<uint32_t *>(base + Ly.segpre);
+    W.votes = reinterpret_cast<int32_t *>(base + Ly.votes);
+    W.novf = status + 1;
+    W.piece_cap = (loop_cap > 0 && loop_cap < piece_cap) ? loop_cap : piece_cap;
+    W.local_cap = (loop_cap > 0 && loop_cap < INT32_MAX) ? (int32_t)loop_cap : 0;
+    return W;
+}
+
+}  // namespace hk
+
 struct hk_ctx {
     int device = 0;
     int ty = 16, tz = 16;
@@ -29,6 +57,7 @@ struct hk_ctx {
     size_t sbuf_bytes = 0;
     int last_cuda = 0;
     int32_t *dstatus = nullptr;   // device status word (STATUS_* flags), survives workspace growth
+    int64_t loop_cap = 0;         // test bound of the capped union-find loops (0: natural bounds)
     // per-pass timing: a ring of event sets, one per timed call
     static constexpr int RING = 64;
     bool timing = false;
@@ -53,37 +82,6 @@ constexpr int DEFAULT_TY = 16, DEFAULT_TZ = 16;
 constexpr int64_t MAX_SITES = (int64_t)1 << 31;
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
-
-struct Layout {
-    size_t mask, codes, cnt, pre, bsum, face, tinfo, parent, key, psize, xcol, ovf, rootbits, segpre, votes, ncl, total;
-};
-
-// votes_cap > 0: also the root bits and the per-cluster votes of the interior/exterior
-// identification (index fields)
-Layout make_layout(const TileInfo &ti, const Plan &P, int64_t votes_cap = 0) {
-    Layout L{};
-    size_t off = 0;
-    auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
-    const int64_t nb = (P.nrows + 4096) / 4096;
-    L.mask = take((size_t)P.ntiles * ti.rows * 4);
-    L.codes = take((size_t)P.ntiles * ti.maxruns * 2);
-    L.cnt = take((size_t)P.nseg);
-    L.pre = take((size_t)(P.nrows + 1) * 4);
-    L.bsum = take((size_t)nb * 4);
-    L.face = take((size_t)P.ntiles * ti.face_stride * 2);
-    L.tinfo = take((size_t)P.ntiles * 16);
-    L.parent = take((size_t)P.piece_cap * 4);
-    L.key = take((size_t)P.piece_cap * 4);
-    L.psize = take((size_t)P.piece_cap * 4);
-    L.xcol = take((size_t)P.ntiles * (ti.rows / 32) * 2 * 4);
-    L.ovf = take((size_t)P.ntiles * 4);
-    L.rootbits = take(votes_cap > 0 ? (size_t)P.nseg * 4 : 0);
-    L.segpre = take(votes_cap > 0 ? (size_t)P.nseg * 4 : 0);
-    L.votes = take((size_t)votes_cap * 4);
-    L.ncl = take((size_t)hk::MAX_LAT_PER_LAUNCH * 8);
-    L.total = off;
-    return L;
-}
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -245,7 +243,7 @@ int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st, bo
         Plan P{0, 0, 0, 0};
         for (int i = chunk_start[c]; i < chunk_start[c + 1]; ++i) add_lattice(ti, lats[i].nx, lats[i].ny, lats[i].nz, P);
         P.piece_cap = P.ntiles * ti.max_boundary;
-        need = std::max(need, make_layout(ti, P, inside ? lats[0].sizes_cap : 0).total);
+        need = std::max(need, hk::make_layout(ti, P, inside ? lats[0].sizes_cap : 0).total);
     }
     int rc = ensure_ws(ctx, need);
     if (rc != HK_OK) return rc;
@@ -286,27 +284,14 @@ int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st, bo
             add_lattice(ti, l.nx, l.ny, l.nz, P);
         }
         P.piece_cap = P.ntiles * ti.max_boundary;
-        const Layout Ly = make_layout(ti, P, inside ? lats[0].sizes_cap : 0);
+        const hk::Layout Ly = hk::make_layout(ti, P, inside ? lats[0].sizes_cap : 0);
         char *base = static_cast<char *>(ctx->ws);
-        Work W;
-        W.mask = reinterpret_cast<uint32_t *>(base + Ly.mask);
-        W.codes = reinterpret_cast<uint16_t *>(base + Ly.codes);
-        W.cnt = reinterpret_cast<uint8_t *>(base + Ly.cnt);
-        W.pre = reinterpret_cast<uint32_t *>(base + Ly.pre);
-        W.bsum = reinterpret_cast<uint32_t *>(base + Ly.bsum);
-        W.face = reinterpret_cast<uint16_t *>(base + Ly.face);
-        W.tinfo = reinterpret_cast<int4 *>(base + Ly.tinfo);
-        W.parent = reinterpret_cast<int32_t *>(base + Ly.parent);
-        W.key = reinterpret_cast<int32_t *>(base + Ly.key);
-        W.psize = reinterpret_cast<int32_t *>(base + Ly.psize);
-        W.xcol = reinterpret_cast<uint32_t *>(base + Ly.xcol);
-        W.status = ctx->dstatus;
-        W.ovf = reinterpret_cast<int32_t *>(base + Ly.ovf);
-        W.rootbits = inside ? reinterpret_cast<uint32_t *>(base + Ly.rootbits) : nullptr;
-        W.segpre = inside ? reinterpret_cast<uint32_t *>(base + Ly.segpre) : nullptr;
-        W.votes = inside ? reinterpret_cast<int32_t *>(base + Ly.votes) : nullptr;
-        W.novf = ctx->dstatus + 1;
-        W.piece_cap = P.piece_cap;
+        Work W = hk::bind_work(base, Ly, ctx->dstatus, P.piece_cap, ctx->loop_cap);
+        if (!inside) {
+            W.rootbits = nullptr;
+            W.segpre = nullptr;
+            W.votes = nullptr;
+        }
         int64_t *slots = reinterpret_cast<int64_t *>(base + Ly.ncl);
         bool chunk_check = false;
         for (int i = 0; i < cn; ++i) {
@@ -426,7 +411,7 @@ size_t hk_workspace_bytes(int nx, int ny, int nz) {
     Plan P{0, 0, 0, 0};
     add_lattice(ti, nx, ny, nz, P);
     P.piece_cap = P.ntiles * ti.max_boundary;
-    return make_layout(ti, P).total;
+    return hk::make_layout(ti, P).total;
 }
 
 int hk_reserve(hk_ctx *ctx, size_t bytes) {
@@ -576,6 +561,13 @@ int hk_set_graphs(hk_ctx *ctx, int enable) {
     return HK_OK;
 }
 
+int hk_set_loop_cap(hk_ctx *ctx, int64_t cap) {
+    if (!ctx || cap < 0) return HK_ERR_ARG;
+    ctx->loop_cap = cap;
+    drop_graphs(ctx);   // captured launches carry the old bound
+    return HK_OK;
+}
+
 int hk_label_host(hk_ctx *ctx, const float *phi_host, int nx, int ny, int nz, const int periodic[3],
                   int32_t *labels_host, int64_t *sizes_host, int64_t sizes_cap, int64_t *hist_host,
                   int64_t *n_clusters_host, void *stream) {
@@ -697,7 +689,10 @@ int hk_sync_status(hk_ctx *ctx, void *stream) {
     if (!ctx->dstatus) return HK_OK;
     int32_t s = 0;
     e = cudaMemcpy(&s, ctx->dstatus, sizeof(s), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemset(ctx->dstatus, 0, sizeof(s));
+    if (e == cudaSuccess && s) {   // cleared on the caller's stream, ahead of its later calls
+        e = cudaMemsetAsync(ctx->dstatus, 0, sizeof(s), static_cast<cudaStream_t>(stream));
+        if (e == cudaSuccess) e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    }
     if (e != cudaSuccess) return fail_cuda(ctx, e);
     return s ? HK_ERR_TIMEOUT : HK_OK;
 }

@@ -72,7 +72,10 @@ struct Work {
     int32_t *votes;     // [sizes_cap] sign votes per cluster (index fields only)
     int32_t *ovf;       // [ntiles] tiles with more runs than the fast tile pass holds
     int32_t *novf;      // [1] entries of ovf (reset by the occupancy pass of every call)
-    int64_t piece_cap;  // entries of parent/key/psize: bounds every union-find path
+    int64_t piece_cap;  // bound of every global union-find loop: the entries of parent/key/psize
+                        // (a path visits distinct pieces), or a lower test bound
+    int32_t local_cap;  // bound of the shared-memory union retries: 0 = the tile's run count,
+                        // > 0 a lower test bound
 };
 
 // Tensor maps of the single-lattice fast path (TMA tile loads of phi and TMA

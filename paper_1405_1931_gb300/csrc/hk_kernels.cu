@@ -295,6 +295,7 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
         }
         S.rbase[r] = rb;
         for (int i = r; i < total; i += NT) S.par[i] = i;
+        const int ucap = (W.local_cap > 0 && W.local_cap < total) ? W.local_cap : total;   // union retry bound
 
         // y- and z-neighbours: one union per overlapping run pair of rows (y-1, y) and
         // (z-1, z).  Both pair lists come from one scan of packed counts (each total
@@ -321,7 +322,7 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
         auto union_pairs = [&](int n) {
             for (int i = tid; i < n; i += NT) {
                 const uint32_t p = (uint32_t)S.aux[i];
-                s_union(S.par, (int)(p >> 16), (int)(p & 0xffffu), total, W.status);
+                s_union(S.par, (int)(p >> 16), (int)(p & 0xffffu), ucap, W.status);
             }
         };
         if (ny_tot + nz_tot <= CAP) {           // block-uniform
@@ -345,11 +346,11 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
         if (g.wrapX || g.wrapY || g.wrapZ) {
             if (m) {
                 if (g.wrapY && ly == g.lastY && ly > 0)
-                    join_rows(S.par, m, rb, S.m[r - ly], S.rbase[r - ly], total, W.status);
+                    join_rows(S.par, m, rb, S.m[r - ly], S.rbase[r - ly], ucap, W.status);
                 if (g.wrapZ && lz == g.lastZ && lz > 0)
-                    join_rows(S.par, m, rb, S.m[r - lz * TY], S.rbase[r - lz * TY], total, W.status);
+                    join_rows(S.par, m, rb, S.m[r - lz * TY], S.rbase[r - lz * TY], ucap, W.status);
                 if (g.wrapX && g.lastX > 0 && (m & 1u) && ((m >> g.lastX) & 1u))
-                    s_union(S.par, rb, run_of(rb, rs, g.lastX), total, W.status);
+                    s_union(S.par, rb, run_of(rb, rs, g.lastX), ucap, W.status);
             }
             __syncthreads();
         }

@@ -34,6 +34,48 @@ struct Plan {
 
 constexpr int NUM_PASSES = 7;   // occupancy, tile_label, face_merge, piece_finalize, scan, lattice_finish, flatten
 
+// Byte offsets of the workspace buffers of one launch (every offset 256-byte aligned).
+struct Layout {
+    size_t mask, codes, cnt, pre, bsum, face, tinfo, parent, key, psize, xcol, ovf, rootbits, segpre, votes, ncl, total;
+};
+
+// The workspace of one launch.  votes_cap > 0: also the root bits, the segment prefix
+// and the per-cluster votes of the interior/exterior identification (index fields).
+inline Layout make_layout(const TileInfo &ti, const Plan &P, int64_t votes_cap = 0) {
+    Layout L{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) & ~(size_t)255;
+        return o;
+    };
+    const int64_t nb = (P.nrows + 4096) / 4096;   // scan blocks (4096 rows each) covering index nrows
+    L.mask = take((size_t)P.ntiles * ti.rows * 4);
+    L.codes = take((size_t)P.ntiles * ti.maxruns * 2);
+    L.cnt = take((size_t)P.nseg);
+    L.pre = take((size_t)(P.nrows + 1) * 4);
+    L.bsum = take((size_t)nb * 4);
+    L.face = take((size_t)P.ntiles * ti.face_stride * 2);
+    L.tinfo = take((size_t)P.ntiles * 16);
+    L.parent = take((size_t)P.piece_cap * 4);
+    L.key = take((size_t)P.piece_cap * 4);
+    L.psize = take((size_t)P.piece_cap * 4);
+    L.xcol = take((size_t)P.ntiles * (ti.rows / 32) * 2 * 4);
+    L.ovf = take((size_t)P.ntiles * 4);
+    L.rootbits = take(votes_cap > 0 ? (size_t)P.nseg * 4 : 0);
+    L.segpre = take(votes_cap > 0 ? (size_t)P.nseg * 4 : 0);
+    L.votes = take((size_t)votes_cap * 4);
+    L.ncl = take((size_t)MAX_LAT_PER_LAUNCH * 8);
+    L.total = off;
+    return L;
+}
+
+// The Work pointers of a workspace laid out by `Ly` at device address `base`.  status:
+// two device int32 words (the STATUS_* flags, then the count of tiles handed to the
+// dense tile pass).  loop_cap > 0 lowers the bound of every capped union-find loop
+// (0: the natural bounds, the run count and the piece-table size).
+Work bind_work(char *base, const Layout &Ly, int32_t *status, int64_t piece_cap, int64_t loop_cap);
+
 bool tile_info(int ty, int tz, TileInfo &ti);
 
 // ev: NUM_PASSES + 1 events recorded around the passes, or nullptr.  tms: the tensor

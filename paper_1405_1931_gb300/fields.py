@@ -81,17 +81,6 @@ def block_field_device(L: int, b: int, device="cuda"):
     return (1 - 2 * par).to(torch.float32)
 
 
-def block_labels_device(L: int, b: int, device="cuda"):
-    """Closed-form labels of block_field_device(L, b): the smallest row-major index of
-    each occupied domain (its corner), -1 for the medium."""
-    import torch
-    c = torch.div(torch.arange(L, device=device, dtype=torch.int32), b, rounding_mode="floor")
-    corner = c * b
-    lab = (corner.view(L, 1, 1) * (L * L) + corner.view(1, L, 1) * L + corner.view(1, 1, L))
-    par = (c.view(L, 1, 1) + c.view(1, L, 1) + c.view(1, 1, L)) & 1
-    return torch.where(par == 0, lab, torch.full_like(lab, -1))
-
-
 def sphere_params(n_spheres: int, box: tuple, seed: int, r_lo: float = 5.0, r_hi: float = 15.0):
     """Centres uniform in the box and radii uniform in [r_lo, r_hi] from stream ``seed``.
 
@@ -162,20 +151,6 @@ def capsule_field(L: int, semi_axes: tuple) -> np.ndarray:
         outside_nb |= ~inside[sl]
     shell = core & outside_nb
     return np.where(shell, np.float32(-1.0), np.float32(1.0)).astype(np.float32)
-
-
-def capsule_interior_count(L: int, semi_axes: tuple) -> int:
-    """Number of interior sites: F <= 1 with all six neighbours F <= 1 (counted directly)."""
-    a = np.asarray(semi_axes, dtype=np.float64)
-    g = np.arange(-1, L + 1, dtype=np.float64) - L / 2.0
-    F = (g / a[2])[:, None, None] ** 2 + (g / a[1])[None, :, None] ** 2 + (g / a[0])[None, None, :] ** 2
-    inside = F <= 1.0
-    core = inside[1:-1, 1:-1, 1:-1].copy()
-    for sl in ((slice(0, -2), slice(1, -1), slice(1, -1)), (slice(2, None), slice(1, -1), slice(1, -1)),
-               (slice(1, -1), slice(0, -2), slice(1, -1)), (slice(1, -1), slice(2, None), slice(1, -1)),
-               (slice(1, -1), slice(1, -1), slice(0, -2)), (slice(1, -1), slice(1, -1), slice(2, None))):
-        core &= inside[sl]
-    return int(core.sum())
 
 
 INDEX_FAR = np.float32(-1.0)      # I_0 < -0.5: far from every membrane (Sec. 6, step 1)

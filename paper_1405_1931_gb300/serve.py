@@ -12,7 +12,9 @@ buffers resident on the device and:
   its own library context, so batches on different workers overlap on the
   device, and requests that arrive while others are on the GPU join the next
   batch as soon as a worker frees up;
-* detects completion with CUDA events and frees the request's memory.
+* detects completion with CUDA events and frees the request's memory; once a
+  worker's stream is idle it reads that context's device status word, and a
+  request whose batch saw a bounded device loop give up is counted as failed.
 
 Latency is reported two ways: from the request's arrival to the host
 observing its completion event, and from its field being ready on the device
@@ -53,6 +55,7 @@ class Request:
     ready_to_done_ms: float = math.nan
     t_done: float = math.nan
     n_clusters: int = -1
+    failed: bool = False             # a bounded device loop gave up in its batch
 
     @property
     def sites(self) -> int:
@@ -166,6 +169,8 @@ class Server:
         used = 0
         peak_used = 0
         done = []
+        failed = 0
+        unchecked = [[] for _ in self.streams]   # completed requests whose status is not yet read
         busy_sites = 0
         t0 = time.perf_counter()
         while pending or ready or inflight:
@@ -184,11 +189,23 @@ class Server:
                             r.phi = None
                             r.out = None
                         done.append(r)
+                    unchecked[w].extend(batch)
                     if not fifo:
                         free.append(w)
                 else:
                     still.append((w, batch, ev))
             inflight = still
+            # The device status word of a worker's context (a bounded loop that gave up)
+            # is read once its stream is idle, so that the read waits for nothing; the
+            # word is sticky, so a give-up fails every request completed since the last read.
+            for w in range(len(self.streams)):
+                if unchecked[w] and not any(iw == w for iw, _, _ in inflight):
+                    rc = hk.hk_sync_status(self.labs[w].ctx, hk._stream_handle(self.streams[w]))
+                    if rc != hk.HK_OK:
+                        for r in unchecked[w]:
+                            r.failed = True
+                        failed += len(unchecked[w])
+                    unchecked[w] = []
             # 2. arrivals, admitted by memory
             while pending and pending[0].arrival <= now and used + pending[0].nbytes() <= self.cap:
                 r = pending.popleft()
@@ -241,5 +258,5 @@ class Server:
                 "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
                 "ready_p50_ms": float(np.percentile(lat_ready, 50)), "ready_p99_ms": float(np.percentile(lat_ready, 99)),
                 "peak_admitted_gb": peak_used / GB, "cap_gb": self.cap / GB,
-                "workers": 1 if fifo else len(self.streams),
+                "workers": 1 if fifo else len(self.streams), "failed": failed,
                 "done": done}

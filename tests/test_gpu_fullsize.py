@@ -19,6 +19,7 @@ import pytest
 
 import oracle
 from paper_1405_1931_gb300 import fields
+import closed_forms
 
 torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
@@ -88,7 +89,7 @@ def test_block_benchmark_1024_closed_form(labeller, b):
     want_hist = torch.zeros(32, dtype=torch.int64, device="cuda")
     want_hist[(b ** 3).bit_length() - 1] = n
     assert torch.equal(hist, want_hist)
-    assert torch.equal(labels, fields.block_labels_device(L, b))
+    assert torch.equal(labels, closed_forms.block_labels_device(L, b))
 
 
 def test_near_max_sites_full_parity(labeller):

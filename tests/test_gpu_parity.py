@@ -270,6 +270,7 @@ def test_batched_more_than_one_launch_chunk(labeller):
         assert n == want[3]
         np.testing.assert_array_equal(labels.cpu().numpy(), want[0])
         np.testing.assert_array_equal(sizes[:n].cpu().numpy(), want[1])
+        np.testing.assert_array_equal(hist.cpu().numpy(), want[2])
 
 
 def test_device_generator_matches_host():

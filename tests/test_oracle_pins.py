@@ -14,6 +14,7 @@ import pytest
 import oracle
 from paper_1405_1931_gb300 import fields
 from brute import bfs_label, relax_label, canonical_from_partition, log2_hist
+import closed_forms
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 PERIODIC_ALL = list(itertools.product((0, 1), repeat=3))
@@ -173,13 +174,13 @@ def test_block_benchmark_pattern(case):
 
 @pytest.mark.parametrize("L,b", [(8, 1), (16, 2), (16, 4), (32, 8)])
 def test_block_benchmark_closed_form_helpers(L, b):
-    """The closed form used at 1024^3 on the GPU (fields.block_field_device / block_labels_device,
+    """The closed form used at 1024^3 on the GPU (fields.block_field_device / closed_forms.block_labels_device,
     run here with torch on the CPU) agrees with the oracle: corner labels, (L/b)^3/2 clusters of b^3."""
     torch = pytest.importorskip("torch")
     from paper_1405_1931_gb300 import fields
     phi = fields.block_field_device(L, b, device="cpu").numpy()
     labels, sizes, hist, n = oracle.label(phi, (1, 1, 1))
-    np.testing.assert_array_equal(labels, fields.block_labels_device(L, b, device="cpu").numpy())
+    np.testing.assert_array_equal(labels, closed_forms.block_labels_device(L, b, device="cpu").numpy())
     assert n == (L // b) ** 3 // 2 and (sizes == b ** 3).all()
     assert hist[(b ** 3).bit_length() - 1] == n
 
@@ -271,7 +272,7 @@ def test_capsule_two_clusters(axes):
     phi = fields.capsule_field(L, axes)
     labels, sizes, hist, n = oracle.label(phi, (1, 1, 1))
     assert n == 2
-    interior = fields.capsule_interior_count(L, axes)
+    interior = closed_forms.capsule_interior_count(L, axes)
     shell = int((phi < 0).sum())
     assert sorted(sizes.tolist()) == sorted([interior, L ** 3 - shell - interior])
     assert labels[0, 0, 0] == 0                        # exterior holds site 0
