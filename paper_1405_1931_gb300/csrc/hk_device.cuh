@@ -106,10 +106,11 @@ struct TileShape {
     static constexpr int R = TY * TZ;            // rows per tile
     static constexpr int SITES = TX * R;
     static constexpr int MAXRUNS = 16 * R;       // at most 16 runs in a 32-site row
-    // Run (and union-pair) capacity of the fast tile pass: 10 runs a row on average,
-    // above the 8 of the densest i.i.d. field (p = 1/2).  Tiles beyond it go to a
-    // second pass sized for MAXRUNS.
-    static constexpr int MR_FAST = 10 * R;
+    // Run (and union-pair) capacity of the fast tile pass: 9 runs a row on average,
+    // above the 8 of the densest i.i.d. field (p = 1/2), and small enough that eight
+    // CTAs of the pass share an SM.  Tiles beyond it go to a second pass sized for
+    // MAXRUNS.
+    static constexpr int MR_FAST = 9 * R;
     static constexpr int NT = R;                 // threads per CTA: one per row
     // Face lists inside a tile's face block: 8 counts (one per face, two unused),
     // then per face the boundary numbers of its emitted connected sites.  Emitted

@@ -183,45 +183,39 @@ __global__ void __launch_bounds__(256) k_occupancy_tma(const __grid_constant__ T
 // --------------------------------------------------------------------------------------
 // K1: tile labelling from the occupancy words (one tile per CTA)
 // --------------------------------------------------------------------------------------
-template <int TY, int TZ, int CAP>
+template <int TY, int TZ, int CAP, int BL>
 struct LabelSmem {
     using SH = TileShape<TY, TZ>;
     uint32_t m[SH::R];                     // occupancy word of each row
-    int rbase[SH::R];                      // first run id of each row
-    int par[CAP];                          // union-find over run ids; see piece_k for the
-                                           // encodings after numbering
-    int aux[CAP];                          // union pair lists, then per root: size + AUX_FACE * (runs
-                                           // with a site connected across a tile face)
+    uint16_t rbase[SH::R];                 // first run id of each row
+    int par[CAP];                          // union-find over run ids; after compression: the root
+    int aux[CAP];                          // union pair lists; then per root: size + AUX_FACE *
+                                           // (runs touching a face); then -1 - k for boundary root k
+    uint16_t desc[CAP];                    // per run: DESC_TOUCH | (tile row << 5) | first x
+    uint16_t blist[BL];                    // run ids of the boundary roots, by boundary number
     uint32_t nylo[TZ], nyhi[TZ];           // neighbour rows across the y faces, per plane
     uint32_t nzlo[TY], nzhi[TY];           // neighbour rows across the z faces, per row
     uint32_t nxlo[SH::R / 32], nxhi[SH::R / 32];   // neighbour columns across the x faces
     uint32_t xo0[SH::R / 32], xol[SH::R / 32];     // this tile's first and last column
     static_assert(TZ <= 16 && TY <= 32 && SH::R / 32 <= 16 && SH::NT >= 64, "face loads use threads 0..63");
+    static_assert(SH::R <= 256 && CAP <= 4096, "desc holds an 8-bit row and run ids fit in 16 bits");
     uint32_t chunkbal[CAP / 32];           // boundary-root ballot of each chunk of 32 run ids
     uint32_t chunkint[CAP / 32];           // interior-root ballot of each chunk
     int chunkpre[CAP / 32];                // boundary roots before each chunk
+    int nbnd;                              // boundary roots of the tile
     int warp_tmp[32];
 };
 
 constexpr int AUX_FACE = 1 << 14;   // > any piece size (a tile has at most 8192 sites)
-constexpr int ROOTPOS = 1 << 16;    // par[root] = ROOTPOS | (row << 5 | x0) marks an interior root
-
-// Decode of par[] after numbering: boundary number of run i's piece, or -1 if interior.
-// par[i] is -1 - k for a boundary root, ROOTPOS | position for an interior root, and
-// the root's run id otherwise.
-__device__ __forceinline__ int piece_k(const int *par, int i) {
-    const int v = par[i];
-    if (v < 0) return -1 - v;
-    if (v >= ROOTPOS) return -1;
-    const int w = par[v];
-    return w < 0 ? -1 - w : -1;
-}
+constexpr int DESC_TOUCH = 1 << 13;  // desc flag: the run has a site connected across a tile face
 
 // Resident CTAs per SM of the fast tile pass (its shared memory and 32 registers a
 // thread allow 2048 threads) and of the pass over the tiles it hands on.
 template <int TY, int TZ, bool FAST>
 struct LabelCfg {
     static constexpr int CAP = FAST ? TileShape<TY, TZ>::MR_FAST : TileShape<TY, TZ>::MAXRUNS;
+    // boundary pieces the fast pass lists (more go to the second pass, which has room for all)
+    static constexpr int BL = FAST && TileShape<TY, TZ>::MAX_BOUNDARY > 512 ? 512 : TileShape<TY, TZ>::MAX_BOUNDARY;
     static constexpr int BLOCKS = FAST ? (2048 / (TY * TZ) < 32 ? 2048 / (TY * TZ) : 32)
                                        : (1280 / (TY * TZ) < 32 ? 1280 / (TY * TZ) : 32);
 };
@@ -234,8 +228,9 @@ __global__ void __launch_bounds__(TY * TZ, (LabelCfg<TY, TZ, FAST>::BLOCKS))
 k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
     using SH = TileShape<TY, TZ>;
     constexpr int R = SH::R, NT = SH::NT, MR = SH::MAXRUNS, CAP = LabelCfg<TY, TZ, FAST>::CAP;
+    constexpr int BL = LabelCfg<TY, TZ, FAST>::BL;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    LabelSmem<TY, TZ, CAP> &S = *reinterpret_cast<LabelSmem<TY, TZ, CAP> *>(smem_raw);
+    LabelSmem<TY, TZ, CAP, BL> &S = *reinterpret_cast<LabelSmem<TY, TZ, CAP, BL> *>(smem_raw);
     const int tid = threadIdx.x;
     const int64_t nwork = FAST ? ntiles : (int64_t)*reinterpret_cast<volatile int32_t *>(W.novf);
 
@@ -293,8 +288,31 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
             if (tid == 0) W.ovf[atomicAdd(W.novf, 1)] = (int32_t)t;
             continue;
         }
-        S.rbase[r] = rb;
-        for (int i = r; i < total; i += NT) S.par[i] = i;
+        S.rbase[r] = (uint16_t)rb;
+        // Each run's own union-find node and its descriptor: position and whether one of
+        // its sites is connected across a tile face with a neighbour tile (the site and
+        // its neighbour there both occupied).
+        if (m) {
+            uint32_t conn = 0;
+            if (ly == 0) conn |= S.nylo[lz];
+            if (ly == g.lastY) conn |= S.nyhi[lz];
+            if (lz == 0) conn |= S.nzlo[ly];
+            if (lz == g.lastZ) conn |= S.nzhi[ly];
+            if ((S.nxlo[r >> 5] >> (r & 31)) & 1u) conn |= 1u;
+            if ((S.nxhi[r >> 5] >> (r & 31)) & 1u) conn |= 1u << g.lastX;
+            conn &= m;
+            uint32_t w = rs;
+            int id = rb;
+            while (w) {
+                const int x0 = __ffs(w) - 1;
+                w &= w - 1;
+                const int len = run_len(m, x0);
+                const bool touch = ((conn >> x0) << (32 - len)) != 0;   // a connected site in the run
+                S.par[id] = id;
+                S.desc[id] = (uint16_t)((touch ? DESC_TOUCH : 0) | (r << 5) | x0);
+                ++id;
+            }
+        }
         const int ucap = (W.local_cap > 0 && W.local_cap < total) ? W.local_cap : total;   // union retry bound
 
         // y- and z-neighbours: one union per overlapping run pair of rows (y-1, y) and
@@ -355,54 +373,30 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
             __syncthreads();
         }
 
-        // full compression, one run id per thread: par[i] = root (the piece's first
-        // run).  The finds are read-only, so storing final roots while others still
-        // search is safe.
+        // Sizes accumulate in aux, which held the pair lists until the unions above.
+        for (int i = 4 * tid; i < total; i += 4 * NT)
+            *reinterpret_cast<int4 *>(&S.aux[i]) = make_int4(0, 0, 0, 0);
+        __syncthreads();
+
+        // Compression and piece sizes, one run id per thread: par[i] = root (the piece's
+        // first run), and the run's length -- plus AUX_FACE if it touches a face -- is
+        // added to its root.  The finds are read-only, so storing final roots while
+        // others still search is safe.  A piece is a boundary piece iff its sum reaches
+        // AUX_FACE (sizes stay below it).
         for (int i = tid; i < total; i += NT) {
-            S.par[i] = s_find_ro(S.par, i);
-            S.aux[i] = 0;
+            const int root = s_find_ro(S.par, i);
+            S.par[i] = root;
+            const int d = S.desc[i];
+            const int len = run_len(S.m[(d >> 5) & 0xff], d & 31);
+            atomicAdd(&S.aux[root], len + ((d & DESC_TOUCH) ? AUX_FACE : 0));
         }
         __syncthreads();
 
-        // piece sizes and boundary marks in one shared add per (row, piece): a piece
-        // is a boundary piece iff one of its runs touches a tile face that has a
-        // neighbour tile, which adds AUX_FACE (sizes are < AUX_FACE)
-        if (m) {
-            uint32_t conn = 0;   // sites of this row connected across a tile face
-            if (ly == 0) conn |= S.nylo[lz];
-            if (ly == g.lastY) conn |= S.nyhi[lz];
-            if (lz == 0) conn |= S.nzlo[ly];
-            if (lz == g.lastZ) conn |= S.nzhi[ly];
-            if ((S.nxlo[r >> 5] >> (r & 31)) & 1u) conn |= 1u;
-            if ((S.nxhi[r >> 5] >> (r & 31)) & 1u) conn |= 1u << g.lastX;
-            conn &= m;
-            uint32_t w = rs;
-            int id = rb;
-            int cur = S.par[id], acc = 0;
-            while (w) {
-                const int x0 = __ffs(w) - 1;
-                w &= w - 1;
-                const int len = run_len(m, x0);
-                const int root = S.par[id];
-                if (root == id) S.par[id] = ROOTPOS | (r << 5) | x0;   // only this thread reads it
-                ++id;
-                const bool touch = ((conn >> x0) << (32 - len)) != 0;   // a connected site in the run
-                if (root != cur) {
-                    atomicAdd(&S.aux[cur], acc);
-                    cur = root;
-                    acc = 0;
-                }
-                acc += len + (touch ? AUX_FACE : 0);
-            }
-            atomicAdd(&S.aux[cur], acc);
-        }
-        __syncthreads();
-
-        // Number the boundary roots in run order (par[root] = -1 - k) and write their
-        // records to the tile's slice of the piece table.  Lanes take consecutive run
-        // ids, so the table stores of a chunk of 32 ids are contiguous; chunks are
-        // counted by ballot and scanned.  Interior roots are kept as a ballot per chunk
-        // for the per-row counts below.
+        // Number the boundary roots in run order and write their records to the tile's
+        // slice of the piece table.  Chunks of 32 run ids are counted by ballot, the chunk
+        // counts scanned by one warp, and the boundary roots listed by number, so that only
+        // they do the record writes.  Interior roots are kept as a ballot per chunk for the
+        // per-row counts below.
         const int base = (int)(t * SH::MAX_BOUNDARY);   // fixed slice of the piece table
         {
             const int lane = tid & 31, wid = tid >> 5;
@@ -410,7 +404,7 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
             const int nchunks = (total + 31) / 32;
             for (int c = wid; c < nchunks; c += NW) {
                 const int i = c * 32 + lane;
-                const bool root = i < total && S.par[i] >= ROOTPOS;
+                const bool root = i < total && S.par[i] == i;
                 const bool bnd = root && S.aux[i] >= AUX_FACE;
                 const uint32_t bb = __ballot_sync(0xffffffffu, bnd);
                 const uint32_t bi = __ballot_sync(0xffffffffu, root && !bnd);
@@ -420,26 +414,51 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
                 }
             }
             __syncthreads();
-            int nb_;
-            const int cpre = block_exscan<NT>(tid < nchunks ? __popc(S.chunkbal[tid]) : 0, S.warp_tmp, nb_);
-            if (tid < nchunks) S.chunkpre[tid] = cpre;
+            if (wid == 0) {   // at most CAP / 32 <= 128 chunks
+                int carry = 0;
+                for (int c0 = 0; c0 < nchunks; c0 += 32) {
+                    const int c = c0 + lane;
+                    const int v = c < nchunks ? __popc(S.chunkbal[c]) : 0;
+                    int inc = v;
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const int u = __shfl_up_sync(0xffffffffu, inc, d);
+                        if (lane >= d) inc += u;
+                    }
+                    if (c < nchunks) S.chunkpre[c] = carry + inc - v;
+                    carry += __shfl_sync(0xffffffffu, inc, 31);
+                }
+                if (lane == 0) S.nbnd = carry;
+            }
             __syncthreads();
+        }
+        const int nb_ = S.nbnd;
+        if (FAST && nb_ > BL) {                 // block-uniform; nothing global written yet
+            if (tid == 0) W.ovf[atomicAdd(W.novf, 1)] = (int32_t)t;
+            continue;
+        }
+        {
+            const int lane = tid & 31, wid = tid >> 5;
+            constexpr int NW = NT / 32;
+            const int nchunks = (total + 31) / 32;
             for (int c = wid; c < nchunks; c += NW) {
                 const uint32_t bal = S.chunkbal[c];
-                if ((bal >> lane) & 1u) {
-                    const int i = c * 32 + lane;
-                    const int k = S.chunkpre[c] + __popc(bal & ((1u << lane) - 1u));
-                    const int pos = S.par[i] & (ROOTPOS - 1);        // row << 5 | x0
-                    const int row = pos >> 5;
-                    const int pid = base + k;
-                    W.parent[pid] = pid;
-                    W.key[pid] = ((g.z0 + row / TY) * L.ny + (g.y0 + row % TY)) * L.nx + g.x0 + (pos & 31);
-                    W.psize[pid] = S.aux[i] & (AUX_FACE - 1);
-                    S.par[i] = -1 - k;
-                }
+                if ((bal >> lane) & 1u)
+                    S.blist[S.chunkpre[c] + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)(c * 32 + lane);
             }
-            if (tid == 0) W.tinfo[t] = make_int4(base, nb_, total, 0);
         }
+        __syncthreads();
+        for (int k = tid; k < nb_; k += NT) {
+            const int i = S.blist[k];
+            const int d = S.desc[i];
+            const int row = (d >> 5) & 0xff;
+            const int pid = base + k;
+            W.parent[pid] = pid;
+            W.key[pid] = ((g.z0 + row / TY) * L.ny + (g.y0 + row % TY)) * L.nx + g.x0 + (d & 31);
+            W.psize[pid] = S.aux[i] & (AUX_FACE - 1);
+            S.aux[i] = -1 - k;                   // from here on: boundary root k
+        }
+        if (tid == 0) W.tinfo[t] = make_int4(base, nb_, total, 0);
         __syncthreads();
 
         // interior roots per row segment (a row's runs span at most two chunks)
@@ -461,19 +480,17 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
             W.cnt[seg] = (uint8_t)interior;
         }
 
-        // one code per run (CODE_* encoding)
+        // one code per run (CODE_* encoding): aux of the run's root is -1 - k for boundary
+        // piece k, else the interior piece's size
         uint16_t *C = W.codes + t * MR;
         for (int i = tid; i < total; i += NT) {
             const int v = S.par[i];
+            const int a = S.aux[v];
             uint16_t c;
-            if (v < 0) {
-                c = (uint16_t)(CODE_BOUNDARY | CODE_ROOT | (-1 - v));
-            } else if (v >= ROOTPOS) {
-                c = (uint16_t)(CODE_ROOT | (S.aux[i] & (AUX_FACE - 1)));
-            } else {
-                const int w2 = S.par[v];
-                c = w2 < 0 ? (uint16_t)(CODE_BOUNDARY | (-1 - w2)) : (uint16_t)(w2 & (ROOTPOS - 1));
-            }
+            if (v == i)
+                c = a < 0 ? (uint16_t)(CODE_BOUNDARY | CODE_ROOT | (-1 - a)) : (uint16_t)(CODE_ROOT | a);
+            else
+                c = a < 0 ? (uint16_t)(CODE_BOUNDARY | (-1 - a)) : (uint16_t)(S.desc[v] & (DESC_TOUCH - 1));
             C[i] = c;
         }
 
@@ -532,7 +549,7 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
                     e &= e - 1;
                     const int row = axis == 0 ? lane * 32 + b : row0;
                     const int x = axis == 0 ? (hi ? g.lastX : 0) : b;
-                    F[j++] = (uint16_t)piece_k(S.par, run_of(S.rbase[row], run_starts(S.m[row]), x));
+                    F[j++] = (uint16_t)(-1 - S.aux[S.par[run_of(S.rbase[row], run_starts(S.m[row]), x)]]);
                 }
                 if (lane == 0) F[SH::OFF_CNT + f] = (uint16_t)n;
             }
@@ -1268,7 +1285,8 @@ static cudaError_t launch_all(const LatDev *lats, int n, const Plan &P, const Wo
         all_tma = all_tma && TB.tm[i].valid;
     }
     constexpr int CAP1 = LabelCfg<TY, TZ, true>::CAP, CAP1B = LabelCfg<TY, TZ, false>::CAP;
-    const size_t smem1 = sizeof(LabelSmem<TY, TZ, CAP1>), smem1b = sizeof(LabelSmem<TY, TZ, CAP1B>);
+    const size_t smem1 = sizeof(LabelSmem<TY, TZ, CAP1, LabelCfg<TY, TZ, true>::BL>);
+    const size_t smem1b = sizeof(LabelSmem<TY, TZ, CAP1B, LabelCfg<TY, TZ, false>::BL>);
     const size_t smem4 = sizeof(FlatSmem<TY, TZ>);
     cudaError_t e;
     // Once per device a process uses: the shared-memory opt-ins (a device attribute of
