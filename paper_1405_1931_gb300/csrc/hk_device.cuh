@@ -317,10 +317,26 @@ __device__ __forceinline__ void join_rows(int *par, uint32_t m, int rb, uint32_t
     }
 }
 
-// Sum of the n bytes at base[start, start + n), read as the aligned 32-bit words that
-// cover them (the bytes outside the range are masked off).  The array must extend to
-// the end of the word holding its last byte.
+// Sum of the first n (<= 8) bytes of w, each at most 16: the multiply adds every byte
+// into the top one, which holds the sum (at most 128).
+__device__ __forceinline__ uint32_t bytes8_sum(uint64_t w, int n) {
+    const uint64_t keep = n >= 8 ? ~0ull : (n <= 0 ? 0ull : (1ull << (8 * n)) - 1ull);
+    return (uint32_t)(((w & keep) * 0x0101010101010101ull) >> 56);
+}
+
+// Sum of the n bytes at base[start, start + n), each at most 16.  A range of at most 32
+// bytes that starts 16-byte aligned (a lattice row of up to 32 segments) is read as two
+// 16-byte loads issued together; any other range as the aligned 32-bit words that cover
+// it (the bytes outside the range are masked off).  The array must extend to the end of
+// the 16-byte block holding its last byte.
 __device__ __forceinline__ uint32_t bytes_sum(const uint8_t *base, int64_t start, int64_t n) {
+    if (n <= 32 && (start & 15) == 0) {
+        if (n <= 0) return 0;
+        const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(base + start);
+        const ulonglong2 b = n > 16 ? *reinterpret_cast<const ulonglong2 *>(base + start + 16) : make_ulonglong2(0, 0);
+        const int k = (int)n;
+        return bytes8_sum(a.x, k) + bytes8_sum(a.y, k - 8) + bytes8_sum(b.x, k - 16) + bytes8_sum(b.y, k - 24);
+    }
     uint32_t s = 0;
     const int64_t e = start + n;
     for (int64_t w = start & ~(int64_t)3; w < e; w += 4) {
