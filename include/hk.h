@@ -144,13 +144,14 @@ typedef struct hk_lattice {
  * HK_ERR_CUDA, HK_ERR_CAPACITY (some lattice overflowed its sizes_cap). */
 int hk_label_batched(hk_ctx *ctx, const hk_lattice *lats, int n, void *stream);
 
-/* Replay batched calls from CUDA graphs.  When enabled, hk_label_batched on a
- * non-default stream, with timing off and every sizes_cap >= ceil(N/2), keeps
- * an instantiated CUDA graph of its launch sequence keyed by the exact
+/* Replay calls from CUDA graphs.  When enabled, hk_label and hk_label_batched on a
+ * non-default stream, with timing off and every sizes_cap >= ceil(N/2), keep
+ * an instantiated CUDA graph of their launch sequence keyed by the exact
  * descriptors (pointers, shapes, periodic flags, capacities) and the tile
- * shape; a later call with the same descriptors replays it (one graph launch
- * instead of one launch per pass).  The first call with new descriptors runs
- * normally and then captures.  Graphs are dropped when the workspace grows,
+ * shape; a later call with the same descriptors (a simulation labelling its
+ * field in place, step after step) replays it: one graph launch instead of one
+ * launch per pass.  The first call with new descriptors runs normally and then
+ * captures.  Graphs are dropped when the workspace grows,
  * when graphs are disabled and by hk_destroy; at most 8 are kept.  Buffers
  * named by a kept graph must stay allocated while it may be replayed.
  * Errors: HK_ERR_ARG. */
@@ -301,6 +302,20 @@ int hk_interior_update_sites(int8_t *state, int64_t n_sites, const int32_t *site
  * the library default.  Applies to later calls on this context.
  * Errors: HK_ERR_ARG for an unsupported shape. */
 int hk_set_tile(hk_ctx *ctx, int ty, int tz);
+
+/* The one-launch path for small lattices.  A lattice of at most 32768 sites and
+ * 2048 row segments of 32 sites along x (nx rounded up to a multiple of 32, times
+ * ny * nz) is labelled by one kernel: one CTA holds the whole lattice in shared
+ * memory and runs every step of hk_label there (occupancy, x-runs, their
+ * union-find with the periodic edges, ranks, sizes, histogram, labels), so a
+ * call is one launch and uses no workspace.  hk_label, hk_label_host(_async)
+ * and hk_label_batched take it when every lattice of the call fits (a batch:
+ * one CTA per lattice, 64 lattices per launch); results are identical to the
+ * tiled passes.  With timing on, such a call reports all its time as the first
+ * pass.  enable == 0 makes this context use the tiled passes for every lattice
+ * (for tests and comparisons).  Enabled by default.  Drops the context's graphs.
+ * Errors: HK_ERR_ARG. */
+int hk_set_small_path(hk_ctx *ctx, int enable);
 
 /* Per-pass timing.  hk_set_timing(ctx, 1) resets the totals and makes every
  * later call record CUDA events on its own stream between its passes (a ring

@@ -58,6 +58,8 @@ struct hk_ctx {
     int last_cuda = 0;
     int32_t *dstatus = nullptr;   // device status word (STATUS_* flags), survives workspace growth
     int64_t loop_cap = 0;         // test bound of the capped union-find loops (0: natural bounds)
+    int64_t *dcounts = nullptr;   // device cluster counts of the one-CTA path when the caller gives none
+    bool small_path = true;       // lattices that fit take the one-CTA path
     // per-pass timing: a ring of event sets, one per timed call
     static constexpr int RING = 64;
     bool timing = false;
@@ -199,6 +201,68 @@ void fold_timing(hk_ctx *ctx, int slot) {
     if (fold_slot(ctx, slot) != cudaSuccess) ctx->timing = false;
 }
 
+int ensure_status(hk_ctx *ctx) {
+    if (ctx->dstatus) return HK_OK;
+    cudaError_t e = cudaMalloc(&ctx->dstatus, 256);
+    if (e != cudaSuccess) { cudaGetLastError(); ctx->dstatus = nullptr; return HK_ERR_NOMEM; }
+    e = cudaMemset(ctx->dstatus, 0, 256);
+    return e == cudaSuccess ? HK_OK : fail_cuda(ctx, e);
+}
+
+// Lattices that all fit the one-CTA path (hk::small_fits), n <= MAX_LAT_PER_LAUNCH: one
+// launch, no workspace.  Same capacity rule and outputs as the tiled path; with timing on,
+// the whole launch counts as the first pass.
+int run_small(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st, bool check_capacity) {
+    int rc = ensure_status(ctx);
+    if (rc != HK_OK) return rc;
+    if (!ctx->dcounts) {
+        cudaError_t e = cudaMalloc(&ctx->dcounts, hk::MAX_LAT_PER_LAUNCH * sizeof(int64_t));
+        if (e != cudaSuccess) { cudaGetLastError(); ctx->dcounts = nullptr; return HK_ERR_NOMEM; }
+    }
+    std::vector<LatDev> dev(n);
+    bool check = false;
+    for (int i = 0; i < n; ++i) {
+        const hk_lattice &l = lats[i];
+        LatDev &d = dev[i];
+        std::memset(&d, 0, sizeof(d));
+        d.phi = l.phi;
+        d.labels = l.labels;
+        d.sizes = l.sizes;
+        d.sizes_cap = l.sizes ? l.sizes_cap : 0;
+        d.hist = l.hist;
+        d.ncl = l.n_clusters ? l.n_clusters : ctx->dcounts + i;
+        d.nx = l.nx; d.ny = l.ny; d.nz = l.nz;
+        for (int a = 0; a < 3; ++a) d.per[a] = l.periodic[a] ? 1 : 0;
+        d.nbx = (int)ceil_div(l.nx, hk::TX);
+        const int64_t N = (int64_t)l.nx * l.ny * l.nz;
+        if (check_capacity && d.sizes_cap < (N + 1) / 2) check = true;
+    }
+    cudaEvent_t *ev = nullptr;
+    if (ctx->timing) {
+        const int slot = (int)(ctx->ncalls % hk_ctx::RING);
+        if (ctx->ncalls - ctx->nacc >= hk_ctx::RING) fold_timing(ctx, slot);
+        ev = ctx->ev[slot];
+        ctx->ncalls += 1;
+        cudaEventRecord(ev[0], st);
+    }
+    const int32_t lcap = (ctx->loop_cap > 0 && ctx->loop_cap < INT32_MAX) ? (int32_t)ctx->loop_cap : 0;
+    cudaError_t e = hk::launch_small(dev.data(), n, ctx->dstatus, lcap, st);
+    if (e != cudaSuccess) return fail_cuda(ctx, e);
+    if (ev)
+        for (int i = 1; i <= hk::NUM_PASSES; ++i) cudaEventRecord(ev[i], st);
+    if (check) {
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return fail_cuda(ctx, e);
+        for (int i = 0; i < n; ++i) {
+            int64_t c = 0;
+            e = cudaMemcpy(&c, dev[i].ncl, sizeof(c), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return fail_cuda(ctx, e);
+            if (c > lats[i].sizes_cap) return HK_ERR_CAPACITY;
+        }
+    }
+    return HK_OK;
+}
+
 // Label lats[0..n) with at most MAX_LAT_PER_LAUNCH lattices per pass sequence.
 // index_field (one lattice only): the lattice is an index field; label its far sites
 // (I < -0.5) and, when inside != nullptr, write the interior/exterior tags of its
@@ -215,6 +279,21 @@ int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st, bo
     }
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return fail_cuda(ctx, e);
+
+    // small lattices: one CTA each, up to MAX_LAT_PER_LAUNCH per launch
+    if (!index_field && ctx->small_path) {
+        bool all_small = true;
+        for (int i = 0; i < n && all_small; ++i) all_small = hk::small_fits(lats[i].nx, lats[i].ny, lats[i].nz);
+        if (all_small) {
+            int rc_cap = HK_OK;
+            for (int c0 = 0; c0 < n; c0 += hk::MAX_LAT_PER_LAUNCH) {
+                const int rc = run_small(ctx, lats + c0, std::min(n - c0, hk::MAX_LAT_PER_LAUNCH), st, check_capacity);
+                if (rc == HK_ERR_CAPACITY) rc_cap = rc;
+                else if (rc != HK_OK) return rc;
+            }
+            return rc_cap;
+        }
+    }
 
     // Launch chunks: at most MAX_LAT_PER_LAUNCH lattices, and few enough tiles that
     // every piece id (tile * max_boundary + k) and every root count fits in 31 bits.
@@ -247,12 +326,8 @@ int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st, bo
     }
     int rc = ensure_ws(ctx, need);
     if (rc != HK_OK) return rc;
-    if (!ctx->dstatus) {
-        e = cudaMalloc(&ctx->dstatus, 256);
-        if (e != cudaSuccess) { cudaGetLastError(); ctx->dstatus = nullptr; return HK_ERR_NOMEM; }
-        e = cudaMemset(ctx->dstatus, 0, 256);
-        if (e != cudaSuccess) return fail_cuda(ctx, e);
-    }
+    rc = ensure_status(ctx);
+    if (rc != HK_OK) return rc;
 
     bool any_check = false;
     std::vector<int64_t> counts(n, 0);
@@ -370,6 +445,58 @@ int host_io(hk_ctx *ctx, int64_t N, int64_t sizes_cap, HostIo &io) {
     return HK_OK;
 }
 
+// Label lats[0..n) as one call, replayed from a cached CUDA graph when graphs are on
+// (non-default stream, timing off, every sizes_cap >= ceil(N/2), so no call waits on
+// the host): the first call with given descriptors runs uncaptured (sizing the
+// workspace and setting kernel attributes), then captures the same launches.
+int run_graphed(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st) {
+    bool graphable = ctx->graphs && st != nullptr && !ctx->timing;
+    for (int i = 0; i < n && graphable; ++i) {
+        const int64_t N = (int64_t)lats[i].nx * lats[i].ny * lats[i].nz;
+        if (check_lattice(lats[i]) != HK_OK || lats[i].sizes_cap < (N + 1) / 2) graphable = false;
+    }
+    if (!graphable) return run_lattices(ctx, lats, n, st);
+
+    auto same = [&](const std::vector<hk_lattice> &key) {
+        if ((int)key.size() != n) return false;
+        for (int i = 0; i < n; ++i) {
+            const hk_lattice &a = key[i], &b = lats[i];
+            if (a.phi != b.phi || a.nx != b.nx || a.ny != b.ny || a.nz != b.nz || a.labels != b.labels ||
+                a.sizes != b.sizes || a.sizes_cap != b.sizes_cap || a.hist != b.hist || a.n_clusters != b.n_clusters ||
+                (a.periodic[0] != 0) != (b.periodic[0] != 0) || (a.periodic[1] != 0) != (b.periodic[1] != 0) ||
+                (a.periodic[2] != 0) != (b.periodic[2] != 0))
+                return false;
+        }
+        return true;
+    };
+    for (auto &g : ctx->gcache)
+        if (g.ty == ctx->ty && g.tz == ctx->tz && same(g.key))
+            return cudaGraphLaunch(g.exec, st) == cudaSuccess ? HK_OK : fail_cuda(ctx, cudaGetLastError());
+
+    int rc = run_lattices(ctx, lats, n, st);
+    if (rc != HK_OK) return rc;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return fail_cuda(ctx, e);
+    rc = run_lattices(ctx, lats, n, st);
+    e = cudaStreamEndCapture(st, &graph);
+    if (rc != HK_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return rc != HK_OK ? rc : fail_cuda(ctx, e);
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail_cuda(ctx, e);
+    if ((int)ctx->gcache.size() >= hk_ctx::MAX_GRAPHS) {
+        cudaGraphExecDestroy(ctx->gcache.front().exec);
+        ctx->gcache.erase(ctx->gcache.begin());
+    }
+    ctx->gcache.push_back({std::vector<hk_lattice>(lats, lats + n), ctx->ty, ctx->tz, exec});
+    return HK_OK;   // this call's results came from the uncaptured run
+}
+
 }  // namespace
 
 extern "C" {
@@ -397,6 +524,7 @@ void hk_destroy(hk_ctx *ctx) {
     if (ctx->io) cudaFree(ctx->io);
     if (ctx->sbuf) cudaFree(ctx->sbuf);
     if (ctx->dstatus) cudaFree(ctx->dstatus);
+    if (ctx->dcounts) cudaFree(ctx->dcounts);
     drop_graphs(ctx);
     for (auto &set : ctx->ev)
         for (auto &e : set)
@@ -433,7 +561,7 @@ int hk_label(hk_ctx *ctx, const float *phi, int nx, int ny, int nz, const int pe
     l.sizes_cap = sizes_cap;
     l.hist = hist_out;
     l.n_clusters = n_clusters_out;
-    return run_lattices(ctx, &l, 1, static_cast<cudaStream_t>(stream));
+    return run_graphed(ctx, &l, 1, static_cast<cudaStream_t>(stream));
 }
 
 int hk_label_interior(hk_ctx *ctx, const float *index, int nx, int ny, int nz, const int periodic[3],
@@ -504,60 +632,20 @@ int hk_interior_update_sites(int8_t *state, int64_t n_sites, const int32_t *site
 int hk_label_batched(hk_ctx *ctx, const hk_lattice *lats, int n, void *stream) {
     if (!ctx || n < 0 || (n > 0 && !lats)) return HK_ERR_ARG;
     if (n == 0) return HK_OK;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    bool graphable = ctx->graphs && st != nullptr && !ctx->timing;
-    for (int i = 0; i < n && graphable; ++i) {
-        const int64_t N = (int64_t)lats[i].nx * lats[i].ny * lats[i].nz;
-        if (check_lattice(lats[i]) != HK_OK || lats[i].sizes_cap < (N + 1) / 2) graphable = false;
-    }
-    if (!graphable) return run_lattices(ctx, lats, n, st);
-
-    auto same = [&](const std::vector<hk_lattice> &key) {
-        if ((int)key.size() != n) return false;
-        for (int i = 0; i < n; ++i) {
-            const hk_lattice &a = key[i], &b = lats[i];
-            if (a.phi != b.phi || a.nx != b.nx || a.ny != b.ny || a.nz != b.nz || a.labels != b.labels ||
-                a.sizes != b.sizes || a.sizes_cap != b.sizes_cap || a.hist != b.hist || a.n_clusters != b.n_clusters ||
-                (a.periodic[0] != 0) != (b.periodic[0] != 0) || (a.periodic[1] != 0) != (b.periodic[1] != 0) ||
-                (a.periodic[2] != 0) != (b.periodic[2] != 0))
-                return false;
-        }
-        return true;
-    };
-    for (auto &g : ctx->gcache)
-        if (g.ty == ctx->ty && g.tz == ctx->tz && same(g.key))
-            return cudaGraphLaunch(g.exec, st) == cudaSuccess ? HK_OK : fail_cuda(ctx, cudaGetLastError());
-
-    // First call with these descriptors: run once uncaptured (sizes the workspace,
-    // sets kernel attributes), then capture the same launch sequence and keep it.
-    int rc = run_lattices(ctx, lats, n, st);
-    if (rc != HK_OK) return rc;
-    cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return fail_cuda(ctx, e);
-    rc = run_lattices(ctx, lats, n, st);
-    e = cudaStreamEndCapture(st, &graph);
-    if (rc != HK_OK || e != cudaSuccess) {
-        if (graph) cudaGraphDestroy(graph);
-        cudaGetLastError();
-        return rc != HK_OK ? rc : fail_cuda(ctx, e);
-    }
-    cudaGraphExec_t exec = nullptr;
-    e = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return fail_cuda(ctx, e);
-    if ((int)ctx->gcache.size() >= hk_ctx::MAX_GRAPHS) {
-        cudaGraphExecDestroy(ctx->gcache.front().exec);
-        ctx->gcache.erase(ctx->gcache.begin());
-    }
-    ctx->gcache.push_back({std::vector<hk_lattice>(lats, lats + n), ctx->ty, ctx->tz, exec});
-    return HK_OK;   // this call's results came from the uncaptured run
+    return run_graphed(ctx, lats, n, static_cast<cudaStream_t>(stream));
 }
 
 int hk_set_graphs(hk_ctx *ctx, int enable) {
     if (!ctx) return HK_ERR_ARG;
     ctx->graphs = enable != 0;
     if (!ctx->graphs) drop_graphs(ctx);
+    return HK_OK;
+}
+
+int hk_set_small_path(hk_ctx *ctx, int enable) {
+    if (!ctx) return HK_ERR_ARG;
+    ctx->small_path = enable != 0;
+    drop_graphs(ctx);
     return HK_OK;
 }
 

@@ -49,6 +49,14 @@ struct LatDev {
     int64_t row0;    // first global row id (z*ny + y)
 };
 
+// The lattices of one launch (a kernel parameter).
+template <int NL>
+struct LatBatch {
+    int n;
+    int pad_;
+    LatDev lat[NL];
+};
+
 // Workspace pointers shared by all passes of one launch.
 struct Work {
     uint32_t *mask;     // [ntiles * R] occupancy words, tile-major (tile t, row r)

@@ -25,13 +25,6 @@
 
 namespace hk {
 
-template <int NL>
-struct LatBatch {
-    int n;
-    int pad_;
-    LatDev lat[NL];
-};
-
 // --------------------------------------------------------------------------------------
 // K0: occupancy.  One warp per tile streams phi row by row (one coalesced 128-byte
 // load per row, 16 rows in flight per warp) and keeps phi > 0 (Sec. 2) as one

@@ -78,6 +78,17 @@ Work bind_work(char *base, const Layout &Ly, int32_t *status, int64_t piece_cap,
 
 bool tile_info(int ty, int tz, TileInfo &ti);
 
+// One-CTA path for small lattices (hk_small.cu): a lattice of at most SMALL_MAX_SITES
+// sites and SMALL_MAX_SEG row segments is labelled by one kernel in shared memory, with
+// no workspace.  Runs never exceed N/2 + nseg/2 <= SMALL_MAX_RUNS.
+constexpr int SMALL_MAX_SITES = 32768;
+constexpr int SMALL_MAX_SEG = 2048;
+constexpr int SMALL_MAX_RUNS = 16384 + 2048;
+bool small_fits(int nx, int ny, int nz);
+// n lattices that all fit, one CTA each (n <= MAX_LAT_PER_LAUNCH); every lat[i].ncl must
+// be a device int64.  status: the device status word; local_cap as in Work.
+cudaError_t launch_small(const LatDev *lats, int n, int32_t *status, int32_t local_cap, cudaStream_t st);
+
 // ev: NUM_PASSES + 1 events recorded around the passes, or nullptr.  tms: the tensor
 // maps of each of the n lattices (valid == 0: that lattice takes the plain-load and
 // plain-store paths), or nullptr for none.

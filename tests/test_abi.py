@@ -73,6 +73,7 @@ def test_host_argument_errors_need_no_gpu():
     assert lib.hk_interior_update_sites(None, 10, None, None, 3, None) == hk.HK_ERR_ARG
     assert lib.hk_interior_update_sites(None, 10, None, None, 0, None) == hk.HK_OK
     assert lib.hk_set_loop_cap(None, 4) == hk.HK_ERR_ARG
+    assert lib.hk_set_small_path(None, 1) == hk.HK_ERR_ARG
 
 
 def test_build_entry_compiles_everything():

@@ -45,6 +45,29 @@ def test_batched_graph_replay_is_exact():
     lab.close()
 
 
+def test_single_lattice_graph_replay_is_exact():
+    """hk_label with graphs on: the first call runs and captures, later calls replay, on the
+    one-CTA path (32^3) and on the tiled passes (64 x 48 x 40)."""
+    from paper_1405_1931_gb300.hk import Labeller
+    lab = Labeller(0)
+    lab.set_graphs(True)
+    s = torch.cuda.Stream()
+    for shape, per in [((32, 32, 32), (1, 1, 1)), ((64, 48, 40), (1, 0, 1))]:
+        phi_np = fields.iid_field(*shape, seed=13, occupancy=0.3116)
+        want = oracle.label(phi_np, per)
+        phi = torch.from_numpy(phi_np).cuda()
+        out = lab.alloc_outputs(phi.shape, phi.device)
+        for call in range(3):
+            out[0].fill_(-7)
+            out[1].fill_(-7)
+            out[2].fill_(-7)
+            with torch.cuda.stream(s):
+                lab.label(phi, per, out=out, stream=s)
+            lab.sync_status(s)
+            _check(out, want, f"{shape} call {call}")
+    lab.close()
+
+
 def test_served_results_equal_alone_and_oracle():
     from paper_1405_1931_gb300 import serve
     from paper_1405_1931_gb300.hk import Labeller

@@ -21,8 +21,11 @@ PERIODIC_ALL = list(itertools.product((0, 1), repeat=3))
 
 @pytest.fixture(scope="module")
 def labeller():
+    """The tiled passes for every lattice (the one-CTA path for small lattices is tested in
+    test_gpu_small.py)."""
     from paper_1405_1931_gb300.hk import Labeller
     lab = Labeller(0)
+    lab.set_small_path(False)
     yield lab
     lab.close()
 
