@@ -42,6 +42,14 @@ struct SmallSmem {
 static_assert(SMALL_MAX_SEG <= 2048 && SMALL_MAX_RUNS <= 65535, "desc holds an 11-bit segment, sb a 16-bit run id");
 static_assert(sizeof(SmallSmem) <= 227 * 1024, "one CTA's shared memory");
 
+// Division by a lattice constant d >= 1 by one multiply: floor(x / d) =
+// (x * ceil(2^32 / d)) >> 32, exact while x * d < 2^32 (here x < 2^16 and d <= 2^15).
+struct FastDiv {
+    uint64_t m;
+    __device__ explicit FastDiv(uint32_t d) : m(((1ull << 32) + d - 1) / d) {}
+    __device__ __forceinline__ uint32_t operator()(uint32_t x) const { return (uint32_t)((x * m) >> 32); }
+};
+
 // the run of segment s (first run id b, occupancy word w) holding bit x
 __device__ __forceinline__ int srun(int b, uint32_t w, int x) { return b + __popc(run_starts(w) & le_mask(x)) - 1; }
 
@@ -85,6 +93,7 @@ __global__ void __launch_bounds__(SNT, 1) k_small_label(const __grid_constant__ 
     constexpr int NW = SNT / 32;
     const int nx = L.nx, ny = L.ny, nz = L.nz, nbx = L.nbx;
     const int nseg = nbx * ny * nz;
+    const FastDiv div_nbx((uint32_t)nbx), div_ny((uint32_t)ny);
     if (tid < 32) S.hist[tid] = 0;
 
     // a1: occupancy words; each warp keeps up to 8 segments' loads in flight
@@ -93,7 +102,7 @@ __global__ void __launch_bounds__(SNT, 1) k_small_label(const __grid_constant__ 
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int s = s0 + NW * j;
-            const int q = s / nbx, x = (s - q * nbx) * 32 + lane;
+            const int q = (int)div_nbx((uint32_t)s), x = (s - q * nbx) * 32 + lane;
             v[j] = (s < nseg && x < nx) ? __ldg(L.phi + (int64_t)q * nx + x) : 0.0f;
         }
 #pragma unroll
@@ -139,7 +148,7 @@ __global__ void __launch_bounds__(SNT, 1) k_small_label(const __grid_constant__ 
         const uint32_t w = S.m[s];
         if (!w) continue;
         const int b = S.sb[s];
-        const int q = s / nbx, bx = s - q * nbx, y = q % ny, z = q / ny;
+        const int q = (int)div_nbx((uint32_t)s), bx = s - q * nbx, z = (int)div_ny((uint32_t)q), y = q - z * ny;
         auto join = [&](int t) {   // every overlap of segment s with segment t
             const uint32_t wt = S.m[t];
             uint32_t os = run_starts(w & wt);
@@ -187,19 +196,17 @@ __global__ void __launch_bounds__(SNT, 1) k_small_label(const __grid_constant__ 
         if (rank < capr) L.sizes[rank] = size;
         ++rank;
         atomicAdd(&S.hist[31 - __clz(size)], 1);
+        const int d = S.desc[i], rs_ = d >> 5, rq = (int)div_nbx((uint32_t)rs_);
+        S.sz[i] = rq * nx + (rs_ - rq * nbx) * 32 + (d & 31);   // from here on: the root's site (its label)
     }
+    __syncthreads();
 
     // a5: labels, one warp per segment, one lane per site
     for (int s = wid; s < nseg; s += NW) {
-        const int q = s / nbx, x = (s - q * nbx) * 32 + lane;
+        const int q = (int)div_nbx((uint32_t)s), x = (s - q * nbx) * 32 + lane;
         if (x >= nx) continue;
         const uint32_t w = S.m[s];
-        int lab = -1;
-        if ((w >> lane) & 1u) {
-            const int root = S.par[srun(S.sb[s], w, lane)];
-            const int d = S.desc[root], rs_ = d >> 5, rq = rs_ / nbx;
-            lab = rq * nx + (rs_ - rq * nbx) * 32 + (d & 31);
-        }
+        const int lab = ((w >> lane) & 1u) ? S.sz[S.par[srun(S.sb[s], w, lane)]] : -1;
         L.labels[(int64_t)q * nx + x] = lab;
     }
     __syncthreads();
