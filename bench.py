@@ -406,12 +406,23 @@ def extra_configs(args, peak):
     lab.set_graphs(False)
     lab.sync_status(s)
     lab.set_tile(16, 16)
+    lab.set_merge(2, 1)
+    # compulsory bytes of the whole batch: 8 B a site, 8 B a cluster size, 256 B of histogram a lattice
+    nclus = sum(int(o[3].item()) for _, _, o in items)
+    bbytes = 8 * sites + 8 * nclus + 256 * len(items)
     res["batched96"] = {"workload": "96 lattices, axes in {32,...,384}, p in U[0.15,0.45], random periodic flags",
-                        "sites": sites, "tile": list(tuned["tile"]), "autotune_ms": tuned["ms"],
+                        "sites": sites, "n_clusters": nclus, "tile": list(tuned["tile"]),
+                        "merge_schedule": {"face_merge_unions_per_lane": tuned["merge"][0],
+                                           "finalize_combines_hot_root": bool(tuned["merge"][1])},
+                        "autotune_ms": tuned["ms"],
                         "per_lattice_ms": per, "batched_ms": bat, "batched_graph_ms": gra,
                         "per_lattice_gsites_per_s": sites / (per * 1e-3) / 1e9,
                         "batched_gsites_per_s": sites / (bat * 1e-3) / 1e9,
-                        "batched_graph_gsites_per_s": sites / (gra * 1e-3) / 1e9}
+                        "batched_graph_gsites_per_s": sites / (gra * 1e-3) / 1e9,
+                        "roofline_frac": {"per_lattice": bbytes / (per * 1e-3) / 1e9 / peak,
+                                          "batched": bbytes / (bat * 1e-3) / 1e9 / peak,
+                                          "batched_graph": bbytes / (gra * 1e-3) / 1e9 / peak,
+                                          "bytes": bbytes}}
     del items
     lab.close()
     torch.cuda.empty_cache()
@@ -429,6 +440,10 @@ def extra_configs(args, peak):
     srv.close()
     for st in (cont, fifo, sat_c, sat_f):
         st.pop("done", None)
+        # compulsory bytes per second of the served stream (8 B a site and 256 B of
+        # histogram a request; the 8 B cluster sizes are left out: droplet fields hold
+        # about one cluster per droplet, far under 0.1 % of the sites)
+        st["roofline_frac"] = (8 * st["sites"] + 256 * st["requests"]) / st["wall_s"] / 1e9 / peak if st["wall_s"] else 0.0
     res["served"] = {"workload": f"{args.served_requests} Poisson requests at 400/s, 80% emulsion / 20% capsule, "
                                  "side log-uniform in [64,512], 32 GB admission cap",
                      "continuous": cont, "fifo": fifo,

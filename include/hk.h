@@ -303,6 +303,20 @@ int hk_interior_update_sites(int8_t *state, int64_t n_sites, const int32_t *site
  * Errors: HK_ERR_ARG for an unsupported shape. */
 int hk_set_tile(hk_ctx *ctx, int ty, int tz);
 
+/* Select the merge schedule of the tiled passes (results are identical for every
+ * schedule; only the time differs):
+ *   unions_per_lane  face merge: unions each lane takes per step, their find chains
+ *                    walked in lockstep so their loads overlap: 1, 2 or 4 (0 = the
+ *                    default, 2);
+ *   combine_hot      piece finalize: 1 (default) combines the size additions of the
+ *                    cluster root that collects most of them -- the percolating
+ *                    cluster's -- per warp and per CTA before the global add; 0 adds
+ *                    each group of lanes' sum directly.
+ * The tile shape (hk_set_tile) and this schedule are what autotune.py searches.
+ * Applies to later calls on this context; drops its graphs.
+ * Errors: HK_ERR_ARG for other values. */
+int hk_set_merge(hk_ctx *ctx, int unions_per_lane, int combine_hot);
+
 /* The one-launch path for small lattices.  A lattice of at most 32768 sites and
  * 2048 row segments of 32 sites along x (nx rounded up to a multiple of 32, times
  * ny * nz) is labelled by one kernel: one CTA holds the whole lattice in shared

@@ -60,6 +60,7 @@ struct hk_ctx {
     int64_t loop_cap = 0;         // test bound of the capped union-find loops (0: natural bounds)
     int64_t *dcounts = nullptr;   // device cluster counts of the one-CTA path when the caller gives none
     bool small_path = true;       // lattices that fit take the one-CTA path
+    hk::MergeSchedule merge;      // unions per lane of the face merge, hot-root combining
     // per-pass timing: a ring of event sets, one per timed call
     static constexpr int RING = 64;
     bool timing = false;
@@ -72,7 +73,7 @@ struct hk_ctx {
         std::vector<hk_lattice> key;
         int ty, tz;
         cudaGraphExec_t exec;
-    };
+    };   // graphs are dropped whenever the schedule changes
     static constexpr int MAX_GRAPHS = 8;
     bool graphs = false;
     std::vector<GraphEntry> gcache;
@@ -384,7 +385,7 @@ int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st, bo
         }
         std::vector<hk::TmapPair> tms(cn);
         for (int i = 0; i < cn; ++i) make_tmaps(lats[c0 + i], ctx->ty, ctx->tz, tms[i]);
-        e = hk::launch_label(ctx->ty, ctx->tz, dev.data(), cn, P, W, tms.data(), st, ev);
+        e = hk::launch_label(ctx->ty, ctx->tz, dev.data(), cn, P, W, tms.data(), st, ev, ctx->merge);
         if (e != cudaSuccess) return fail_cuda(ctx, e);
         if (inside && dev[0].sizes_cap > 0) {
             e = hk::launch_interior(dev[0], W, st, state);
@@ -639,6 +640,17 @@ int hk_set_graphs(hk_ctx *ctx, int enable) {
     if (!ctx) return HK_ERR_ARG;
     ctx->graphs = enable != 0;
     if (!ctx->graphs) drop_graphs(ctx);
+    return HK_OK;
+}
+
+int hk_set_merge(hk_ctx *ctx, int unions_per_lane, int combine_hot) {
+    if (!ctx) return HK_ERR_ARG;
+    if (unions_per_lane == 0) unions_per_lane = 2;
+    if (unions_per_lane != 1 && unions_per_lane != 2 && unions_per_lane != 4) return HK_ERR_ARG;
+    if (combine_hot != 0 && combine_hot != 1) return HK_ERR_ARG;
+    ctx->merge.unions = unions_per_lane;
+    ctx->merge.hot = combine_hot;
+    drop_graphs(ctx);
     return HK_OK;
 }
 

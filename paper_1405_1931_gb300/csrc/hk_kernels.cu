@@ -554,15 +554,16 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
 // --------------------------------------------------------------------------------------
 // K2: face merge.  One warp per tile: its low face lists along x, y and z are joined
 // entry by entry with the high face lists of its lower neighbours (for tile 0 of a
-// periodic axis: the last tile, the wrap).  Each lane takes U entries at a time and
+// periodic axis: the last tile, the wrap).  Each lane takes U entries at a time (a
+// merge-schedule parameter: 1, 2 or 4) and
 // walks the finds of all their endpoints in lockstep, so their loads are in flight
 // together; the roots are then linked by CAS, and a lost CAS falls back to g_union.
 // --------------------------------------------------------------------------------------
-template <int TY, int TZ, int NL>
+template <int TY, int TZ, int NL, int U>
 __global__ void __launch_bounds__(256)
 k_face_merge(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
     using SH = TileShape<TY, TZ>;
-    constexpr int U = 2, C = 2 * U;   // unions and chains per lane and step
+    constexpr int C = 2 * U;   // U unions, 2 U find chains per lane and step
     const int lane = threadIdx.x & 31;
     const int64_t t = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (t >= ntiles) return;
@@ -634,10 +635,11 @@ k_face_merge(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
 
 // --------------------------------------------------------------------------------------
 // K3: piece finalize (one warp per tile, one piece per lane).  Size additions into
-// the same cluster root are combined per warp first, because the percolating
-// cluster collects pieces from most tiles.
+// the same cluster root are combined per group of lanes; with HOT (a merge-schedule
+// parameter) the root that collects most of them -- the percolating cluster's -- is
+// further combined per warp and per CTA, because it collects pieces from most tiles.
 // --------------------------------------------------------------------------------------
-template <int NL>
+template <int NL, bool HOT>
 __global__ void __launch_bounds__(256)
 k_piece_finalize(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
     __shared__ int hot_target[8];   // per warp: the cluster root its pieces fed most, and the sum
@@ -678,7 +680,7 @@ k_piece_finalize(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles)
             const unsigned peers = __match_any_sync(0xffffffffu, target);
             const int sum = (int)__reduce_add_sync(peers, (unsigned)add);
             const bool leader = target >= 0 && lane == __ffs(peers) - 1;
-            if (hot < 0) {   // warp-uniform: the first chunk names the warp's hot root (its largest group)
+            if (HOT && hot < 0) {   // warp-uniform: the first chunk names the warp's hot root (its largest group)
                 const unsigned key = leader ? ((unsigned)__popc(peers) << 5) | (unsigned)lane : 0u;
                 const unsigned best = __reduce_max_sync(0xffffffffu, key);
                 if (best) hot = __shfl_sync(0xffffffffu, target, (int)(best & 31u));
@@ -689,6 +691,7 @@ k_piece_finalize(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles)
             }
         }
     }
+    if (!HOT) return;
     hot_acc = (int)__reduce_add_sync(0xffffffffu, (unsigned)hot_acc);
     if (lane == 0) {
         hot_target[wid] = hot;
@@ -1263,7 +1266,7 @@ static int persistent_grid(K kernel, int threads, size_t smem, int64_t ntiles) {
 
 template <int TY, int TZ, int NL>
 static cudaError_t launch_all(const LatDev *lats, int n, const Plan &P, const Work &W, const TmapPair *tms,
-                              cudaStream_t st, cudaEvent_t *ev) {
+                              cudaStream_t st, cudaEvent_t *ev, MergeSchedule ms) {
     using SH = TileShape<TY, TZ>;
     LatBatch<NL> B;
     B.n = n;
@@ -1330,9 +1333,13 @@ static cudaError_t launch_all(const LatDev *lats, int n, const Plan &P, const Wo
     k_tile_label<TY, TZ, NL, false><<<(unsigned)(P.ntiles < grid1b ? P.ntiles : grid1b), SH::NT, smem1b, st>>>(
         B, W, P.ntiles);
     mark(2);
-    k_face_merge<TY, TZ, NL><<<(unsigned)((P.ntiles + 7) / 8), 256, 0, st>>>(B, W, P.ntiles);
+    const unsigned gm = (unsigned)((P.ntiles + 7) / 8);
+    if (ms.unions == 1) k_face_merge<TY, TZ, NL, 1><<<gm, 256, 0, st>>>(B, W, P.ntiles);
+    else if (ms.unions == 4) k_face_merge<TY, TZ, NL, 4><<<gm, 256, 0, st>>>(B, W, P.ntiles);
+    else k_face_merge<TY, TZ, NL, 2><<<gm, 256, 0, st>>>(B, W, P.ntiles);
     mark(3);
-    k_piece_finalize<NL><<<(unsigned)((P.ntiles + 7) / 8), 256, 0, st>>>(B, W, P.ntiles);
+    if (ms.hot) k_piece_finalize<NL, true><<<gm, 256, 0, st>>>(B, W, P.ntiles);
+    else k_piece_finalize<NL, false><<<gm, 256, 0, st>>>(B, W, P.ntiles);
     mark(4);
     const int64_t nb = (P.nrows + SCAN_CH) / SCAN_CH;   // covers index nrows (the total)
     k_scan_reduce<NL><<<(unsigned)nb, SCAN_NT, 0, st>>>(B, W.cnt, P.nrows, W.bsum);
@@ -1348,9 +1355,9 @@ static cudaError_t launch_all(const LatDev *lats, int n, const Plan &P, const Wo
 
 template <int TY, int TZ>
 static cudaError_t launch_shape(const LatDev *lats, int n, const Plan &P, const Work &W, const TmapPair *tms,
-                                cudaStream_t st, cudaEvent_t *ev) {
-    if (n == 1) return launch_all<TY, TZ, 1>(lats, n, P, W, tms, st, ev);
-    return launch_all<TY, TZ, MAX_LAT_PER_LAUNCH>(lats, n, P, W, tms, st, ev);
+                                cudaStream_t st, cudaEvent_t *ev, MergeSchedule ms) {
+    if (n == 1) return launch_all<TY, TZ, 1>(lats, n, P, W, tms, st, ev, ms);
+    return launch_all<TY, TZ, MAX_LAT_PER_LAUNCH>(lats, n, P, W, tms, st, ev, ms);
 }
 
 template <int TY, int TZ>
@@ -1373,11 +1380,11 @@ bool tile_info(int ty, int tz, TileInfo &ti) {
 }
 
 cudaError_t launch_label(int ty, int tz, const LatDev *lats, int n, const Plan &P, const Work &W, const TmapPair *tms,
-                         cudaStream_t st, cudaEvent_t *ev) {
-    if (ty == 8 && tz == 8) return launch_shape<8, 8>(lats, n, P, W, tms, st, ev);
-    if (ty == 16 && tz == 8) return launch_shape<16, 8>(lats, n, P, W, tms, st, ev);
-    if (ty == 16 && tz == 16) return launch_shape<16, 16>(lats, n, P, W, tms, st, ev);
-    if (ty == 32 && tz == 8) return launch_shape<32, 8>(lats, n, P, W, tms, st, ev);
+                         cudaStream_t st, cudaEvent_t *ev, MergeSchedule ms) {
+    if (ty == 8 && tz == 8) return launch_shape<8, 8>(lats, n, P, W, tms, st, ev, ms);
+    if (ty == 16 && tz == 8) return launch_shape<16, 8>(lats, n, P, W, tms, st, ev, ms);
+    if (ty == 16 && tz == 16) return launch_shape<16, 16>(lats, n, P, W, tms, st, ev, ms);
+    if (ty == 32 && tz == 8) return launch_shape<32, 8>(lats, n, P, W, tms, st, ev, ms);
     return cudaErrorInvalidValue;
 }
 

@@ -89,11 +89,19 @@ bool small_fits(int nx, int ny, int nz);
 // be a device int64.  status: the device status word; local_cap as in Work.
 cudaError_t launch_small(const LatDev *lats, int n, int32_t *status, int32_t local_cap, cudaStream_t st);
 
+// The merge schedule: unions per lane and step of the face merge (1, 2 or 4), and
+// whether the piece finalize combines the size additions of the cluster root that
+// collects most of them per warp and per CTA (hot) or adds each group's directly.
+struct MergeSchedule {
+    int unions = 2;
+    int hot = 1;
+};
+
 // ev: NUM_PASSES + 1 events recorded around the passes, or nullptr.  tms: the tensor
 // maps of each of the n lattices (valid == 0: that lattice takes the plain-load and
 // plain-store paths), or nullptr for none.
 cudaError_t launch_label(int ty, int tz, const LatDev *lats, int n, const Plan &P, const Work &W,
-                         const TmapPair *tms, cudaStream_t st, cudaEvent_t *ev);
+                         const TmapPair *tms, cudaStream_t st, cudaEvent_t *ev, MergeSchedule ms = MergeSchedule());
 
 // Interior/exterior tags of a lattice labelled with occ_mode 1 (after launch_label on
 // the same stream; needs W.rootbits and W.votes).

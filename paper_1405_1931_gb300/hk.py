@@ -21,7 +21,7 @@ HK_ERR_CUDA, HK_ERR_TIMEOUT, HK_ERR_NOMEM = 4, 5, 6
 
 EXPORTED = ("hk_create", "hk_destroy", "hk_workspace_bytes", "hk_reserve", "hk_label", "hk_label_batched",
             "hk_label_host", "hk_label_host_async", "hk_set_tile", "hk_set_timing", "hk_get_timing", "hk_sync_status", "hk_set_graphs", "hk_last_cuda_error", "hk_strerror", "hk_label_noalloc",
-            "hk_noalloc_sync_status", "hk_set_loop_cap", "hk_set_small_path",
+            "hk_noalloc_sync_status", "hk_set_loop_cap", "hk_set_small_path", "hk_set_merge",
             "hk_label_interior", "hk_rc_histogram", "hk_interior_state", "hk_interior_update",
             "hk_interior_update_sites",
             "hk_gen_iid", "hk_gen_spheres", "hk_gen_spheres_dev", "hk_gen_capsule")
@@ -69,6 +69,7 @@ def load():
             "hk_noalloc_sync_status": (I, [P]),
             "hk_set_loop_cap": (I, [P, I64]),
             "hk_set_small_path": (I, [P, I]),
+            "hk_set_merge": (I, [P, I, I]),
             "hk_label_interior": (I, [P, P, I, I, I, P, P, P, I64, P, P, P, P]),
             "hk_rc_histogram": (I, [P, P, I64, P, I, P, P, I, P]),
             "hk_interior_state": (I, [P, P, I, I, I, P, P, P]),
@@ -199,6 +200,10 @@ def hk_set_loop_cap(ctx, cap: int) -> int:
     return load().hk_set_loop_cap(ctx, int(cap))
 
 
+def hk_set_merge(ctx, unions_per_lane: int, combine_hot: int) -> int:
+    return load().hk_set_merge(ctx, int(unions_per_lane), int(combine_hot))
+
+
 def hk_set_small_path(ctx, enable: bool) -> int:
     return load().hk_set_small_path(ctx, int(bool(enable)))
 
@@ -279,6 +284,7 @@ class Labeller:
         self.device = int(device)
         self.ctx = hk_create(self.device)
         self.tile = (16, 16)
+        self.merge = (2, 1)
         if tile is not None:
             self.set_tile(*tile)
 
@@ -303,6 +309,13 @@ class Labeller:
         rc = hk_set_graphs(self.ctx, enable)
         if rc != HK_OK:
             raise HKError(rc, "hk_set_graphs")
+
+    def set_merge(self, unions_per_lane: int = 2, combine_hot: int = 1):
+        """Merge schedule of the tiled passes (face-merge unions per lane, hot-root combining)."""
+        rc = hk_set_merge(self.ctx, unions_per_lane, combine_hot)
+        if rc != HK_OK:
+            raise HKError(rc, "hk_set_merge")
+        self.merge = (unions_per_lane or 2, combine_hot)
 
     def set_small_path(self, enable: bool = True):
         """Let lattices that fit take the one-CTA path (default), or force the tiled passes."""

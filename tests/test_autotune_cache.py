@@ -1,5 +1,5 @@
-"""Host logic of the tile-shape autotuner on the CPU: batch signatures and the cache
-path (a cached batch sets its shape without timing anything)."""
+"""Host logic of the autotuner on the CPU: batch signatures and the cache path (a
+cached batch sets its tile shape and merge schedule without timing anything)."""
 import json
 
 import pytest
@@ -21,17 +21,29 @@ def test_signature_rounds_to_powers_of_two():
     assert autotune.signature(items([(64, 64, 64)])) != autotune.signature(items([(64, 64, 128)]))
 
 
-def test_cached_batch_sets_its_shape(tmp_path):
+def test_cached_batch_sets_its_schedule(tmp_path):
     batch = items([(32, 48, 64)])
     cache = tmp_path / "tune.json"
-    cache.write_text(json.dumps({autotune.signature(batch): {"tile": [32, 8], "ms": {"32x8": 1.0}}}))
+    cache.write_text(json.dumps({autotune.signature(batch): {"tile": [32, 8], "merge": [4, 0],
+                                                              "ms": {"32x8/u4h0": 1.0}}}))
 
     class Lab:
         tile = None
+        merge = None
 
         def set_tile(self, ty, tz):
             self.tile = (ty, tz)
 
+        def set_merge(self, u, h):
+            self.merge = (u, h)
+
     lab = Lab()
     got = autotune.tune(lab, batch, cache=str(cache))
     assert got["cached"] and got["tile"] == (32, 8) and lab.tile == (32, 8)
+    assert got["merge"] == (4, 0) and lab.merge == (4, 0)
+
+
+def test_candidates_cover_every_tile_and_schedule():
+    assert set(autotune.TILES) == {(8, 8), (16, 8), (16, 16), (32, 8)}
+    assert {u for u, _ in autotune.MERGES} == {1, 2, 4} and {h for _, h in autotune.MERGES} == {0, 1}
+    assert autotune.DEFAULT_MERGE in autotune.MERGES
