@@ -427,18 +427,23 @@ def extra_configs(args, peak):
     lab.close()
     torch.cuda.empty_cache()
 
-    # served: Poisson stream, continuous batching vs one launch per request
+    # served: Poisson stream, continuous batching vs one launch per request.  The
+    # stand-in simulation hands over each field finished at its request's arrival
+    # (generated up to 50 ms ahead); the same stream with each field generated only
+    # after its request arrives is reported beside it.
     reqs = serve.request_stream(args.served_requests, rate=400.0, seed=3)
     srv = serve.Server(0, cap_bytes=32 * serve.GB, workers=4)
     cont = srv.serve(reqs)
     reqs = serve.request_stream(args.served_requests, rate=400.0, seed=3)
     fifo = srv.serve(reqs, mode="fifo")
+    cont0 = srv.serve(serve.request_stream(args.served_requests, rate=400.0, seed=3), gen_lead_s=0.0)
+    fifo0 = srv.serve(serve.request_stream(args.served_requests, rate=400.0, seed=3), mode="fifo", gen_lead_s=0.0)
     # saturated: the same mix arriving far faster than it can be served
     nsat = max(100, args.served_requests // 4)
     sat_c = srv.serve(serve.request_stream(nsat, rate=20000.0, seed=4))
     sat_f = srv.serve(serve.request_stream(nsat, rate=20000.0, seed=4), mode="fifo")
     srv.close()
-    for st in (cont, fifo, sat_c, sat_f):
+    for st in (cont, fifo, cont0, fifo0, sat_c, sat_f):
         st.pop("done", None)
         # compulsory bytes per second of the served stream (8 B a site and 256 B of
         # histogram a request; the 8 B cluster sizes are left out: droplet fields hold
@@ -447,6 +452,7 @@ def extra_configs(args, peak):
     res["served"] = {"workload": f"{args.served_requests} Poisson requests at 400/s, 80% emulsion / 20% capsule, "
                                  "side log-uniform in [64,512], 32 GB admission cap",
                      "continuous": cont, "fifo": fifo,
+                     "generated_on_arrival": {"continuous": cont0, "fifo": fifo0},
                      "saturated": {"workload": f"{nsat} requests of the same mix at 20000/s",
                                    "continuous": sat_c, "fifo": sat_f}}
     torch.cuda.empty_cache()

@@ -1,17 +1,19 @@
 """Serving loop: labelling requests from a running simulation, continuous batching.
 
 A producer stands in for the simulation (Sec. 5 emulsions and Sec. 6
-capsules): at each request's arrival time it generates the request's field
-on the device, on its own stream.  The server keeps fields and output
+capsules): it generates each request's field on the device, on its own
+stream, finishing about when the request arrives (the simulation hands over a
+finished field).  The server keeps fields and output
 buffers resident on the device and:
 
-* admits arrived requests while their bytes (field, labels, sizes and the
-  per-lattice workspace bound) fit under a memory cap;
-* packs every admitted request whose field is ready into one batched call
-  (``hk_label_batched``) on the first free worker stream -- each worker owns
-  its own library context, so batches on different workers overlap on the
-  device, and requests that arrive while others are on the GPU join the next
-  batch as soon as a worker frees up;
+* admits requests while their bytes (field, labels, sizes and the per-lattice
+  workspace bound) fit under a memory cap;
+* batches by size: arrived small requests go together into one batched call
+  (``hk_label_batched``) on a free high-priority worker stream, large requests
+  run one per call on the other workers -- each worker owns its own library
+  context, so calls on different workers overlap on the device, and requests
+  that arrive while others are on the GPU join the next batch as soon as a
+  worker frees up;
 * detects completion with CUDA events and frees the request's memory; once a
   worker's stream is idle it reads that context's device status word, and a
   request whose batch saw a bounded device loop give up is counted as failed.
@@ -136,31 +138,86 @@ def generate(req: Request, stream) -> None:
 
 
 class Server:
+    """Continuous-batching server of labelling requests on one GPU.
+
+    Workers are library contexts, each on its own stream, above the producers'
+    priority; `small_workers` of them run at a still higher priority and take
+    only small requests (at most `small_sites` sites), batched together up to
+    `max_batch` requests and `small_batch_sites` sites, so that a small request
+    never waits behind a large one and its kernels are scheduled ahead of a large
+    call already on the GPU.  The other workers take large requests, oldest
+    first, one per call; while one is running a second starts only when more
+    than `large_backlog` large requests wait (at low load each large request
+    has the GPU to itself, under load they overlap).  They take small batches
+    when no small worker is free and no large request waits.  The FIFO baseline
+    uses one large-request worker.
+    """
+
     def __init__(self, device: int = 0, cap_bytes: int = 32 * GB, workers: int = 4, max_batch: int = 64,
                  max_batch_sites: int = 1 << 28, tile: tuple | None = None, graphs: bool = False,
-                 producers: int = 4):
+                 producers: int = 4, small_workers: int = 2, small_sites: int = 1 << 21,
+                 small_batch_sites: int = 1 << 23, large_backlog: int = 1, small_priority: int = -2,
+                 max_side: int = 512):
         import torch
         self.device = device
         self.cap = cap_bytes
         self.max_batch = max_batch
         self.max_batch_sites = max_batch_sites   # bounds each worker's workspace
+        self.small_sites = small_sites
+        self.small_batch_sites = small_batch_sites
+        self.large_backlog = large_backlog
+        self.n_small = max(0, min(small_workers, workers - 1))
+        # Priorities (a lower number is a higher one, clamped to the device's range): the
+        # simulation stand-in's producers run at the default, every labelling worker above
+        # them, and the small-request workers above the large ones.
         self.producers = [torch.cuda.Stream(device=device) for _ in range(producers)]
-        self.streams = [torch.cuda.Stream(device=device) for _ in range(workers)]
+        self.streams = ([torch.cuda.Stream(device=device, priority=small_priority) for _ in range(self.n_small)] +
+                        [torch.cuda.Stream(device=device, priority=-1) for _ in range(workers - self.n_small)])
         self.labs = [hk.Labeller(device, tile=tile) for _ in range(workers)]
         for lab in self.labs:
             if graphs:
                 lab.set_graphs(True)
+        self.warm(max_side)
+
+    def warm(self, max_side: int):
+        """Grow every worker's workspace for the largest request (a cube of max_side) and
+        for a full small batch, and run one small call on each worker, so that no call
+        in service allocates (a cudaMalloc synchronises the device) or sets up kernels."""
+        import torch
+        need = hk.hk_workspace_bytes(max_side, max_side, max_side)
+        side = max(1, int(round(self.small_batch_sites ** (1.0 / 3.0))))
+        need = max(need, hk.hk_workspace_bytes(side, side, side) * 2)
+        phi = torch.full((48, 48, 40), -1.0, dtype=torch.float32, device=f"cuda:{self.device}")
+        phi[::2] = 1.0
+        for lab, s in zip(self.labs, self.streams):
+            lab.reserve(need)
+            out = lab.alloc_outputs(phi.shape, phi.device)
+            with torch.cuda.stream(s):
+                lab.label(phi, (1, 1, 1), out=out, stream=s)
+                lab.label_batched([(phi, (1, 1, 1), out), (phi, (0, 1, 0), lab.alloc_outputs(phi.shape, phi.device))],
+                                  stream=s)
+            lab.sync_status(s)
 
     def close(self):
         for lab in self.labs:
             lab.close()
 
-    def serve(self, requests: list, mode: str = "continuous", keep_outputs: bool = False) -> dict:
-        """Serve `requests` (arrival times in seconds from now) and return statistics."""
+    def serve(self, requests: list, mode: str = "continuous", keep_outputs: bool = False,
+              gen_lead_s: float = 0.05) -> dict:
+        """Serve `requests` (arrival times in seconds from now) and return statistics.
+
+        The stand-in simulation produces each request's field on a producer stream
+        starting `gen_lead_s` before the request's arrival (as memory admits), so that
+        a request arrives when the simulation hands over its finished field; a field
+        still being written at arrival is waited for on the device.  gen_lead_s = 0
+        generates each field only once its request has arrived.  Latency is from
+        arrival to the host seeing the request's labels done.
+        """
         import torch
         spheres_dev = upload_spheres(requests)   # noqa: F841  (kept alive for the run)
         pending = deque(sorted(requests, key=lambda r: r.arrival))
-        ready = deque()          # admitted, field generation issued, not yet launched
+        generated = deque()      # field generation issued, request not yet arrived
+        ready = deque()          # arrived, not yet launched
         inflight = []            # (worker, [requests], end_event)
         # continuous batching uses every worker; the baseline is one launch per
         # request, in arrival order, on a single stream
@@ -171,9 +228,9 @@ class Server:
         done = []
         failed = 0
         unchecked = [[] for _ in self.streams]   # completed requests whose status is not yet read
-        busy_sites = 0
+        nprod = 0
         t0 = time.perf_counter()
-        while pending or ready or inflight:
+        while pending or generated or ready or inflight:
             now = time.perf_counter() - t0
             # 1. completions
             still = []
@@ -206,57 +263,112 @@ class Server:
                             r.failed = True
                         failed += len(unchecked[w])
                     unchecked[w] = []
-            # 2. arrivals, admitted by memory
-            while pending and pending[0].arrival <= now and used + pending[0].nbytes() <= self.cap:
+            # 2. the simulation produces fields ahead of their arrival, admitted by memory
+            while pending and pending[0].arrival - gen_lead_s <= now and used + pending[0].nbytes() <= self.cap:
                 r = pending.popleft()
                 used += r.nbytes()
                 peak_used = max(peak_used, used)
-                prod = self.producers[r.rid % len(self.producers)]
+                prod = self.producers[nprod % len(self.producers)]
+                nprod += 1
                 with torch.cuda.stream(prod):
                     generate(r, prod)
                     r.out = hk.Labeller.alloc_outputs(r.phi.shape, r.phi.device)
                     r.gen_event = torch.cuda.Event(enable_timing=True)
                     r.gen_event.record(prod)
-                ready.append(r)
-            # 3. launches
+                generated.append(r)
+            # 3. arrivals
+            while generated and generated[0].arrival <= now:
+                ready.append(generated.popleft())
+            # 4. launches
             if ready and (free or fifo):
-                # fifo: every request is its own launch, enqueued back to back on stream 0
-                w = 0 if fifo else free.pop(0)
-                s = self.streams[w]
                 if fifo:
-                    batch = [ready.popleft()]
+                    # every request is its own launch, enqueued back to back on one
+                    # large-request worker stream
+                    w, batch = self.n_small, [ready.popleft()]
                 else:
-                    batch = [ready.popleft()]
-                    sites = batch[0].sites
-                    while ready and len(batch) < self.max_batch and sites + ready[0].sites <= self.max_batch_sites:
-                        sites += ready[0].sites
-                        batch.append(ready.popleft())
-                for r in batch:
-                    s.wait_event(r.gen_event)
-                with torch.cuda.stream(s):
-                    if len(batch) == 1:
-                        r = batch[0]
-                        self.labs[w].label(r.phi, r.periodic, out=r.out, stream=s)
-                    else:
-                        self.labs[w].label_batched([(r.phi, r.periodic, r.out) for r in batch], stream=s)
-                    ev = torch.cuda.Event(enable_timing=True)
-                    ev.record(s)
-                busy_sites += sum(r.sites for r in batch)
-                inflight.append((w, batch, ev))
-                continue
-            if not inflight and not ready and pending:
-                wait = pending[0].arrival - (time.perf_counter() - t0)
+                    w, batch = self._pick(ready, free)
+                if batch:
+                    s = self.streams[w]
+                    for r in batch:
+                        s.wait_event(r.gen_event)
+                    with torch.cuda.stream(s):
+                        if len(batch) == 1:
+                            r = batch[0]
+                            self.labs[w].label(r.phi, r.periodic, out=r.out, stream=s)
+                        else:
+                            self.labs[w].label_batched([(r.phi, r.periodic, r.out) for r in batch], stream=s)
+                        ev = torch.cuda.Event(enable_timing=True)
+                        ev.record(s)
+                    inflight.append((w, batch, ev))
+                    continue
+            nxt = []
+            if pending:
+                nxt.append(pending[0].arrival - gen_lead_s)
+            if generated:
+                nxt.append(generated[0].arrival)
+            if not inflight and not ready and nxt:
+                wait = min(nxt) - (time.perf_counter() - t0)
                 if wait > 0:
                     time.sleep(min(wait, 0.001))
         wall = max(r.t_done for r in done) if done else 0.0
         lat = np.array([r.t_done - r.arrival for r in done]) * 1e3
         lat_ready = np.array([r.ready_to_done_ms for r in done])
         sites = sum(r.sites for r in done)
-        return {"mode": mode, "requests": len(done), "wall_s": wall, "sites": sites,
-                "gsites_per_s": sites / wall / 1e9 if wall > 0 else 0.0,
-                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
-                "ready_p50_ms": float(np.percentile(lat_ready, 50)), "ready_p99_ms": float(np.percentile(lat_ready, 99)),
-                "peak_admitted_gb": peak_used / GB, "cap_gb": self.cap / GB,
-                "workers": 1 if fifo else len(self.streams), "failed": failed,
-                "done": done}
+        small = np.array([r.sites <= self.small_sites for r in done])
+        stats = {"mode": mode, "requests": len(done), "wall_s": wall, "sites": sites,
+                 "gsites_per_s": sites / wall / 1e9 if wall > 0 else 0.0,
+                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                 "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+                 "ready_p50_ms": float(np.percentile(lat_ready, 50)), "ready_p99_ms": float(np.percentile(lat_ready, 99)),
+                 "peak_admitted_gb": peak_used / GB, "cap_gb": self.cap / GB,
+                 "workers": 1 if fifo else len(self.streams), "failed": failed, "gen_lead_ms": gen_lead_s * 1e3,
+                 "done": done}
+        if small.any() and (~small).any():
+            stats["small_p99_ms"] = float(np.percentile(lat[small], 99))
+            stats["large_p99_ms"] = float(np.percentile(lat[~small], 99))
+        return stats
+
+    def _pick(self, ready: deque, free: list):
+        """Continuous mode: the next batch for a free worker, or (-1, []) to wait.
+
+        Small requests go to a free small worker (high priority) as one batch, oldest
+        first, up to max_batch requests and small_batch_sites sites; large requests go
+        to a free large worker one at a time, oldest first; a free large worker with no
+        large request waiting takes a small batch."""
+        small_free = [w for w in free if w < self.n_small]
+        large_free = [w for w in free if w >= self.n_small]
+        has_small = any(r.sites <= self.small_sites for r in ready)
+        has_large = any(r.sites > self.small_sites for r in ready)
+
+        def take_small():
+            batch, sites = [], 0
+            for r in list(ready):
+                if r.sites > self.small_sites:
+                    continue
+                if batch and (len(batch) >= self.max_batch or sites + r.sites > self.small_batch_sites):
+                    break
+                batch.append(r)
+                sites += r.sites
+            for r in batch:
+                ready.remove(r)
+            return batch
+
+        if has_small and small_free:
+            w = small_free[0]
+            free.remove(w)
+            return w, take_small()
+        # large requests one at a time while the GPU keeps up (each gets the whole GPU,
+        # as in FIFO); a second and later large worker only when large ones queue up
+        n_large_busy = (len(self.streams) - self.n_small) - len(large_free)
+        n_large_ready = sum(1 for r in ready if r.sites > self.small_sites)
+        if has_large and large_free and (n_large_busy == 0 or n_large_ready > self.large_backlog):
+            w = large_free[0]
+            free.remove(w)
+            r = next(r for r in ready if r.sites > self.small_sites)
+            ready.remove(r)
+            return w, [r]
+        if has_small and large_free and not has_large:
+            w = large_free[0]
+            free.remove(w)
+            return w, take_small()
+        return -1, []

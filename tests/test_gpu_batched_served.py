@@ -91,6 +91,37 @@ def test_served_results_equal_alone_and_oracle():
     lab.close()
 
 
+def test_served_mix_up_to_256_equals_alone_and_oracle():
+    """Small requests mixed with ones of several hundred thousand to 16 M sites (sides
+    log-uniform in [24, 256], fields ready at arrival and generated on arrival): every
+    result equals labelling the request alone; the largest three and the smallest three
+    also equal the oracle."""
+    from paper_1405_1931_gb300 import serve
+    from paper_1405_1931_gb300.hk import Labeller
+    srv = serve.Server(0, cap_bytes=8 * serve.GB, workers=4, max_side=256)
+    lab = Labeller(0)
+    for lead in (0.05, 0.0):
+        reqs = serve.request_stream(20, rate=2000.0, seed=17, l_lo=24, l_hi=256)
+        stats = srv.serve(reqs, keep_outputs=True, gen_lead_s=lead)
+        assert stats["requests"] == 20 and stats["failed"] == 0
+        done = sorted(stats["done"], key=lambda r: r.sites)
+        assert done[-1].L >= 150 and done[0].L <= 40          # a real mix of sizes
+        for r in done:
+            alone = lab.alloc_outputs(r.phi.shape, r.phi.device)
+            lab.label(r.phi, r.periodic, out=alone)
+            torch.cuda.synchronize()
+            n = int(alone[3].item())
+            assert int(r.out[3].item()) == n == r.n_clusters
+            assert torch.equal(r.out[0], alone[0])
+            assert torch.equal(r.out[1][:n], alone[1][:n])
+            assert torch.equal(r.out[2], alone[2])
+        if lead > 0:
+            for r in done[:3] + done[-3:]:
+                _check(r.out, oracle.label(r.phi.cpu().numpy(), r.periodic), f"request {r.rid} L={r.L}")
+    lab.close()
+    srv.close()
+
+
 def test_served_fifo_matches_continuous():
     from paper_1405_1931_gb300 import serve
     a = serve.Server(0, cap_bytes=1 * serve.GB, workers=2, max_batch=6)
