@@ -144,6 +144,75 @@ typedef struct hk_lattice {
  * HK_ERR_CUDA, HK_ERR_CAPACITY (some lattice overflowed its sizes_cap). */
 int hk_label_batched(hk_ctx *ctx, const hk_lattice *lats, int n, void *stream);
 
+/* ---- A lattice split into slabs along z across ranks (Sec. 3) -------------------
+ * The domain decomposition of Sec. 3: each rank (one GPU, one context) holds planes
+ * [z0, z0 + nz) of an nx * ny * NZ lattice, labels them, and the ranks merge the
+ * clusters that cross the slab faces.  Every label is a site index of the whole
+ * lattice, so labels are unique without Eq. 1's per-process offsets.  The caller moves
+ * the face data between ranks (paper_1405_1931_gb300/distributed.py does it with
+ * torch.distributed); every rank then resolves all equivalences itself, which replaces
+ * the gather at a root process and the scatter.  Per rank, on one stream:
+ *   1. hk_label_slab: labels of the slab's clusters (the x and y periodic edges apply
+ *      inside the slab; z joins across slabs in step 3), their sizes, and each
+ *      cluster's label (smallest site) in the same rank order;
+ *   2. hk_slab_faces: the face clusters (clusters with a site on the slab's first or
+ *      last plane), numbered 0 .. n_face - 1 in no particular order, with their labels
+ *      and sizes, and for each site of the two face planes its face cluster or -1;
+ *   3. the caller gathers every rank's face arrays, counts and lists, then
+ *      hk_slab_merge: joins facing sites of consecutive slabs (and of the last and
+ *      first slab when z is periodic) into classes, rewrites this slab's labels to the
+ *      class label (the smallest site of the whole cluster), and writes the sizes of
+ *      the clusters whose smallest site is in this slab, in label order, with their
+ *      floor(log2 size) histogram;
+ *   4. the caller adds the own counts of the earlier ranks to place this rank's sizes
+ *      in the global order, and sums the histograms.
+ * The results equal hk_label on the whole lattice: the concatenated slabs' labels, the
+ * ranks' size lists in rank order, the summed histograms and counts.  Not tested on
+ * several GPUs: the tests run two ranks on one GPU, exchanging through the host. */
+
+/* Step 1.  phi: device float32[nz][ny][nx], the slab's planes z0 .. z0 + nz - 1 of a
+ * lattice with (z0 + nz) * nx * ny < 2^31 sites up to the slab.  labels_out: device
+ * int32[nz][ny][nx], labels as site indices of the whole lattice (-1 medium).
+ * sizes_out (int64) and roots_out (int32): device, sizes_cap >= ceil(nx*ny*nz / 2)
+ * entries; cluster k's size and label, k in label order.  n_clusters_out: device int64.
+ * Asynchronous.  Errors: HK_ERR_ARG (null pointers, bad dimensions, smaller sizes_cap),
+ * HK_ERR_TOO_LARGE, HK_ERR_NOMEM, HK_ERR_CUDA. */
+int hk_label_slab(hk_ctx *ctx, const float *phi, int nx, int ny, int nz, int64_t z0, int periodic_x, int periodic_y,
+                  int32_t *labels_out, int64_t *sizes_out, int64_t sizes_cap, int32_t *roots_out,
+                  int64_t *n_clusters_out, void *stream);
+
+/* Step 2, after step 1 on the same context and stream (the arguments are step 1's
+ * outputs).  face_out: device int32[2][ny][nx], the face-cluster number of each site of
+ * plane 0 and plane nz - 1 of the slab, or -1 for the medium.  list_lab_out (int32) and
+ * list_size_out (int64): device, 2 * nx * ny entries; the label and size of face cluster
+ * f.  n_face_out: device int64, the number of face clusters.  The context keeps each
+ * local cluster's face-cluster number for step 3.  Asynchronous.
+ * Errors: HK_ERR_ARG, HK_ERR_NOMEM, HK_ERR_CUDA. */
+int hk_slab_faces(hk_ctx *ctx, const int32_t *labels, int nx, int ny, int nz, const int32_t *roots,
+                  const int64_t *sizes, const int64_t *n_clusters, int64_t sizes_cap, int32_t *face_out,
+                  int32_t *list_lab_out, int64_t *list_size_out, int64_t *n_face_out, void *stream);
+
+/* Step 3, after step 2 on the same context, with the face data of all nranks ranks in
+ * rank order (rank r holds planes after those of rank r - 1):
+ *   face_all       device int32[nranks][2][ny][nx]: every rank's face_out;
+ *   n_face_all     host int64[nranks]: every rank's n_face;
+ *   list_lab_all   device int32[nranks][max_face], list_size_all device int64[nranks][max_face]:
+ *                  every rank's lists, each padded to max_face >= every n_face;
+ *   labels         this rank's labels (step 1), rewritten in place; nz, z0 its slab;
+ *   sizes, n_clusters, sizes_cap: this rank's step-1 sizes and count;
+ *   own_sizes_out  device int64[own_cap]: the sizes of the clusters whose smallest site
+ *                  lies in this slab, in label order (a cluster that crosses slabs is
+ *                  listed once, by the slab of its smallest site, with its whole size);
+ *   own_n_out      device int64: their number (own_cap >= n_clusters always suffices);
+ *   hist_out       device int64[32]: their floor(log2 size) histogram.
+ * Synchronises the stream at its end.  Errors: HK_ERR_ARG (bad counts, step 2 missing),
+ * HK_ERR_TOO_LARGE (2^31 face clusters or more), HK_ERR_NOMEM, HK_ERR_CUDA. */
+int hk_slab_merge(hk_ctx *ctx, int nranks, int rank, int periodic_z, int nx, int ny, const int32_t *face_all,
+                  const int64_t *n_face_all, const int32_t *list_lab_all, const int64_t *list_size_all,
+                  int64_t max_face, int32_t *labels, int nz, int64_t z0, const int64_t *sizes,
+                  const int64_t *n_clusters, int64_t sizes_cap, int64_t *own_sizes_out, int64_t own_cap,
+                  int64_t *own_n_out, int64_t *hist_out, void *stream);
+
 /* Replay calls from CUDA graphs.  When enabled, hk_label and hk_label_batched on a
  * non-default stream, with timing off and every sizes_cap >= ceil(N/2), keep
  * an instantiated CUDA graph of their launch sequence keyed by the exact

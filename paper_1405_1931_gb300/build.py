@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libhk.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["hk_kernels.cu", "hk_small.cu", "hk_api.cu", "hk_gen.cu", "hk_noalloc.cu", "hk_stats.cu"]
+SOURCES = ["hk_kernels.cu", "hk_small.cu", "hk_slab.cu", "hk_api.cu", "hk_gen.cu", "hk_noalloc.cu", "hk_stats.cu"]
 
 
 def nvcc() -> str:

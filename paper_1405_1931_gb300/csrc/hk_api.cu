@@ -41,6 +41,8 @@ Work bind_work(char *base, const Layout &Ly, int32_t *status, int64_t piece_cap,
     W.novf = status + 1;
     W.piece_cap = (loop_cap > 0 && loop_cap < piece_cap) ? loop_cap : piece_cap;
     W.local_cap = (loop_cap > 0 && loop_cap < INT32_MAX) ? (int32_t)loop_cap : 0;
+    W.site_off = 0;
+    W.roots = nullptr;
     return W;
 }
 
@@ -61,6 +63,10 @@ struct hk_ctx {
     int64_t *dcounts = nullptr;   // device cluster counts of the one-CTA path when the caller gives none
     bool small_path = true;       // lattices that fit take the one-CTA path
     hk::MergeSchedule merge;      // unions per lane of the face merge, hot-root combining
+    void *slab_fmap = nullptr;    // face-cluster number of each local cluster (hk_slab_faces -> hk_slab_merge)
+    size_t slab_fmap_bytes = 0;
+    void *slab_merge = nullptr;   // scratch of hk_slab_merge
+    size_t slab_merge_bytes = 0;
     // per-pass timing: a ring of event sets, one per timed call
     static constexpr int RING = 64;
     bool timing = false;
@@ -202,6 +208,23 @@ void fold_timing(hk_ctx *ctx, int slot) {
     if (fold_slot(ctx, slot) != cudaSuccess) ctx->timing = false;
 }
 
+int grow(void *&buf, size_t &have, size_t need) {
+    if (need <= have) return HK_OK;
+    if (buf) {
+        cudaDeviceSynchronize();
+        cudaFree(buf);
+        buf = nullptr;
+        have = 0;
+    }
+    if (cudaMalloc(&buf, need) != cudaSuccess) {
+        cudaGetLastError();
+        buf = nullptr;
+        return HK_ERR_NOMEM;
+    }
+    have = need;
+    return HK_OK;
+}
+
 int ensure_status(hk_ctx *ctx) {
     if (ctx->dstatus) return HK_OK;
     cudaError_t e = cudaMalloc(&ctx->dstatus, 256);
@@ -271,7 +294,8 @@ int run_small(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st, bool 
 // check_capacity == false: never wait for the counts (the caller compares them).
 // state != nullptr (index fields with inside): also the interior state of every site.
 int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st, bool index_field = false,
-                 int8_t *inside = nullptr, bool check_capacity = true, int8_t *state = nullptr) {
+                 int8_t *inside = nullptr, bool check_capacity = true, int8_t *state = nullptr,
+                 int64_t site_off = 0, int32_t *roots = nullptr) {
     TileInfo ti;
     if (!hk::tile_info(ctx->ty, ctx->tz, ti)) return HK_ERR_ARG;
     for (int i = 0; i < n; ++i) {
@@ -282,7 +306,7 @@ int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st, bo
     if (e != cudaSuccess) return fail_cuda(ctx, e);
 
     // small lattices: one CTA each, up to MAX_LAT_PER_LAUNCH per launch
-    if (!index_field && ctx->small_path) {
+    if (!index_field && ctx->small_path && !roots && site_off == 0) {
         bool all_small = true;
         for (int i = 0; i < n && all_small; ++i) all_small = hk::small_fits(lats[i].nx, lats[i].ny, lats[i].nz);
         if (all_small) {
@@ -368,6 +392,8 @@ int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st, bo
             W.segpre = nullptr;
             W.votes = nullptr;
         }
+        W.site_off = site_off;   // slab calls: one lattice
+        W.roots = roots;
         int64_t *slots = reinterpret_cast<int64_t *>(base + Ly.ncl);
         bool chunk_check = false;
         for (int i = 0; i < cn; ++i) {
@@ -526,6 +552,8 @@ void hk_destroy(hk_ctx *ctx) {
     if (ctx->sbuf) cudaFree(ctx->sbuf);
     if (ctx->dstatus) cudaFree(ctx->dstatus);
     if (ctx->dcounts) cudaFree(ctx->dcounts);
+    if (ctx->slab_fmap) cudaFree(ctx->slab_fmap);
+    if (ctx->slab_merge) cudaFree(ctx->slab_merge);
     drop_graphs(ctx);
     for (auto &set : ctx->ev)
         for (auto &e : set)
@@ -634,6 +662,118 @@ int hk_label_batched(hk_ctx *ctx, const hk_lattice *lats, int n, void *stream) {
     if (!ctx || n < 0 || (n > 0 && !lats)) return HK_ERR_ARG;
     if (n == 0) return HK_OK;
     return run_graphed(ctx, lats, n, static_cast<cudaStream_t>(stream));
+}
+
+int hk_label_slab(hk_ctx *ctx, const float *phi, int nx, int ny, int nz, int64_t z0, int periodic_x, int periodic_y,
+                  int32_t *labels_out, int64_t *sizes_out, int64_t sizes_cap, int32_t *roots_out,
+                  int64_t *n_clusters_out, void *stream) {
+    if (!ctx || !phi || !labels_out || !sizes_out || !roots_out || !n_clusters_out) return HK_ERR_ARG;
+    if (nx < 1 || ny < 1 || nz < 1 || z0 < 0) return HK_ERR_ARG;
+    const int64_t N = (int64_t)nx * ny * nz;
+    if ((z0 + nz) * (int64_t)nx * ny >= MAX_SITES) return HK_ERR_TOO_LARGE;
+    if (sizes_cap < (N + 1) / 2) return HK_ERR_ARG;
+    hk_lattice l;
+    l.phi = phi;
+    l.nx = nx; l.ny = ny; l.nz = nz;
+    l.periodic[0] = periodic_x ? 1 : 0;
+    l.periodic[1] = periodic_y ? 1 : 0;
+    l.periodic[2] = 0;   // z joins across the slabs (hk_slab_merge)
+    l.labels = labels_out;
+    l.sizes = sizes_out;
+    l.sizes_cap = sizes_cap;
+    l.hist = nullptr;
+    l.n_clusters = n_clusters_out;
+    return run_lattices(ctx, &l, 1, static_cast<cudaStream_t>(stream), false, nullptr, false, nullptr,
+                        z0 * (int64_t)nx * ny, roots_out);
+}
+
+int hk_slab_faces(hk_ctx *ctx, const int32_t *labels, int nx, int ny, int nz, const int32_t *roots,
+                  const int64_t *sizes, const int64_t *n_clusters, int64_t sizes_cap, int32_t *face_out,
+                  int32_t *list_lab_out, int64_t *list_size_out, int64_t *n_face_out, void *stream) {
+    if (!ctx || !labels || !roots || !sizes || !n_clusters || !face_out || !list_lab_out || !list_size_out ||
+        !n_face_out)
+        return HK_ERR_ARG;
+    if (nx < 1 || ny < 1 || nz < 1 || sizes_cap < 1) return HK_ERR_ARG;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return fail_cuda(ctx, e);
+    int rc = grow(ctx->slab_fmap, ctx->slab_fmap_bytes, (size_t)sizes_cap * sizeof(int32_t));
+    if (rc != HK_OK) return rc;
+    e = hk::launch_slab_faces(labels, nx, ny, nz, roots, n_clusters, sizes, sizes_cap,
+                              static_cast<int32_t *>(ctx->slab_fmap), face_out, list_lab_out, list_size_out,
+                              n_face_out, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? HK_OK : fail_cuda(ctx, e);
+}
+
+int hk_slab_merge(hk_ctx *ctx, int nranks, int rank, int periodic_z, int nx, int ny, const int32_t *face_all,
+                  const int64_t *n_face_all, const int32_t *list_lab_all, const int64_t *list_size_all,
+                  int64_t max_face, int32_t *labels, int nz, int64_t z0, const int64_t *sizes,
+                  const int64_t *n_clusters, int64_t sizes_cap, int64_t *own_sizes_out, int64_t own_cap,
+                  int64_t *own_n_out, int64_t *hist_out, void *stream) {
+    if (!ctx || nranks < 1 || rank < 0 || rank >= nranks || !face_all || !n_face_all || !labels || !sizes ||
+        !n_clusters || !own_n_out || !hist_out || max_face < 0 || own_cap < 0 || (own_cap > 0 && !own_sizes_out))
+        return HK_ERR_ARG;
+    if (nx < 1 || ny < 1 || nz < 1 || z0 < 0 || sizes_cap < 1) return HK_ERR_ARG;
+    if (max_face > 0 && (!list_lab_all || !list_size_all)) return HK_ERR_ARG;
+    if (!ctx->slab_fmap || ctx->slab_fmap_bytes < (size_t)sizes_cap * sizeof(int32_t)) return HK_ERR_ARG;
+    std::vector<int64_t> off(nranks), cnt(nranks);
+    int64_t G = 0;
+    for (int r = 0; r < nranks; ++r) {
+        if (n_face_all[r] < 0 || n_face_all[r] > max_face) return HK_ERR_ARG;
+        off[r] = G;
+        cnt[r] = n_face_all[r];
+        G += n_face_all[r];
+    }
+    if (G >= ((int64_t)1 << 31)) return HK_ERR_TOO_LARGE;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return fail_cuda(ctx, e);
+    int rc = ensure_status(ctx);
+    if (rc != HK_OK) return rc;
+    // scratch: off, cnt (R each), parent, lab (G int32), size, csize (G int64), bsum
+    const int64_t nb = sizes_cap / 4096 + 1;
+    const size_t o_off = 0, o_cnt = align256(8 * (size_t)nranks), o_par = o_cnt + align256(8 * (size_t)nranks);
+    const size_t o_lab = o_par + align256(4 * (size_t)G), o_size = o_lab + align256(4 * (size_t)G);
+    const size_t o_csize = o_size + align256(8 * (size_t)G), o_bsum = o_csize + align256(8 * (size_t)G);
+    const size_t need = o_bsum + align256(4 * (size_t)nb);
+    rc = grow(ctx->slab_merge, ctx->slab_merge_bytes, need);
+    if (rc != HK_OK) return rc;
+    char *b = static_cast<char *>(ctx->slab_merge);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    e = cudaMemcpyAsync(b + o_off, off.data(), 8 * (size_t)nranks, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_cnt, cnt.data(), 8 * (size_t)nranks, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return fail_cuda(ctx, e);
+    hk::SlabMerge M;
+    M.R = nranks;
+    M.ninterfaces = nranks - 1 + (periodic_z ? 1 : 0);
+    M.P = (int64_t)nx * ny;
+    M.maxF = max_face;
+    M.G = G;
+    M.g0 = off[rank];
+    M.nf_own = cnt[rank];
+    M.face_all = face_all;
+    M.list_lab_all = list_lab_all;
+    M.list_size_all = list_size_all;
+    M.off = reinterpret_cast<int64_t *>(b + o_off);
+    M.cnt = reinterpret_cast<int64_t *>(b + o_cnt);
+    M.parent = reinterpret_cast<int32_t *>(b + o_par);
+    M.lab = reinterpret_cast<int32_t *>(b + o_lab);
+    M.size = reinterpret_cast<int64_t *>(b + o_size);
+    M.csize = reinterpret_cast<int64_t *>(b + o_csize);
+    M.labels = labels;
+    M.nsites = (int64_t)nx * ny * nz;
+    M.site_off = z0 * (int64_t)nx * ny;
+    M.sizes = sizes;
+    M.ncl = n_clusters;
+    M.ncl_cap = sizes_cap;
+    M.fmap = static_cast<const int32_t *>(ctx->slab_fmap);
+    M.bsum = reinterpret_cast<uint32_t *>(b + o_bsum);
+    M.own_sizes = own_sizes_out;
+    M.own_cap = own_cap;
+    M.own_ncl = own_n_out;
+    M.hist = hist_out;
+    M.status = ctx->dstatus;
+    e = hk::launch_slab_merge(M, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // off and cnt are host arrays of this call
+    return e == cudaSuccess ? HK_OK : fail_cuda(ctx, e);
 }
 
 int hk_set_graphs(hk_ctx *ctx, int enable) {

@@ -84,6 +84,11 @@ struct Work {
                         // (a path visits distinct pieces), or a lower test bound
     int32_t local_cap;  // bound of the shared-memory union retries: 0 = the tile's run count,
                         // > 0 a lower test bound
+    // one slab of a lattice split along z (single-lattice launches only): added to every
+    // label, the index of the slab's first site in the whole lattice (else 0); and, when
+    // not null, the label of each cluster in rank order (sizes_cap entries, like sizes)
+    int64_t site_off;
+    int32_t *roots;
 };
 
 // Tensor maps of the single-lattice fast path (TMA tile loads of phi and TMA

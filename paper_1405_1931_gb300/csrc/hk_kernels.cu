@@ -919,6 +919,8 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapBa
         const int site_row = ((g.z0 + lz) * L.ny + (g.y0 + ly)) * L.nx + g.x0;
         const int site_row0 = (g.z0 * L.ny + g.y0) * L.nx + g.x0, sxy_i = L.nx * L.ny;
         uint32_t rootbits = 0;                // first sites of cluster roots in this row
+        const int soff = (int)W.site_off;     // labels of a slab are sites of the whole lattice
+        const bool want_labels = W.roots != nullptr;
         uint32_t w = rs;
         int id = rb;
         while (w) {
@@ -938,10 +940,13 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapBa
             const int crow = ci >> 5;
             const int own = site_row + x0;
             const int other = site_row0 + (crow / TY) * sxy_i + (crow % TY) * L.nx + (ci & 31);
-            const int lab = isb ? gl : (isr ? own : other);
+            const int lab = (isb ? gl : (isr ? own : other)) + soff;
             const int size = isr ? (isb ? gs : k) : -1;
             if (size > 0) {
-                if (rank < L.sizes_cap) L.sizes[rank] = size;
+                if (rank < L.sizes_cap) {
+                    L.sizes[rank] = size;
+                    if (want_labels) W.roots[rank] = lab;
+                }
                 ++rank;
                 rootbits |= 1u << x0;
                 atomicAdd(&S.hist[31 - __clz(size)], 1);

@@ -103,6 +103,34 @@ struct MergeSchedule {
 cudaError_t launch_label(int ty, int tz, const LatDev *lats, int n, const Plan &P, const Work &W,
                          const TmapPair *tms, cudaStream_t st, cudaEvent_t *ev, MergeSchedule ms = MergeSchedule());
 
+// The slab merge (hk_slab.cu): the face data of all R ranks and this rank's slab.
+struct SlabMerge {
+    int R;                          // ranks (slabs)
+    int ninterfaces;                // R - 1, plus one when z is periodic (slab R - 1 to slab 0)
+    int64_t P;                      // sites of a z plane, nx * ny
+    int64_t maxF;                   // row length of the gathered face-cluster lists
+    int64_t G;                      // face clusters of all ranks
+    int64_t g0, nf_own;             // this rank's first node and its face-cluster count
+    const int32_t *face_all;        // [R][2][P] face-cluster number of each face site, or -1
+    const int32_t *list_lab_all;    // [R][maxF] labels of the face clusters
+    const int64_t *list_size_all;   // [R][maxF] local sizes of the face clusters
+    const int64_t *off, *cnt;       // [R] device: first node and face-cluster count of each rank
+    int32_t *parent, *lab;          // [G] scratch
+    int64_t *size, *csize;          // [G] scratch
+    int32_t *labels;                // this slab's labels, rewritten in place
+    int64_t nsites, site_off;       // sites of the slab and the index of its first site
+    const int64_t *sizes, *ncl;     // this slab's local cluster sizes and count (device)
+    int64_t ncl_cap;                // entries of sizes / fmap
+    const int32_t *fmap;            // [ncl_cap] face-cluster number of each local cluster, or -1
+    uint32_t *bsum;                 // [ncl_cap / 4096 + 1] scratch
+    int64_t *own_sizes, own_cap, *own_ncl, *hist;   // outputs
+    int32_t *status;
+};
+cudaError_t launch_slab_faces(const int32_t *labels, int nx, int ny, int nzr, const int32_t *roots, const int64_t *ncl,
+                              const int64_t *sizes, int64_t ncl_cap, int32_t *fmap, int32_t *face_out,
+                              int32_t *list_lab, int64_t *list_size, int64_t *nf, cudaStream_t st);
+cudaError_t launch_slab_merge(const SlabMerge &M, cudaStream_t st);
+
 // Interior/exterior tags of a lattice labelled with occ_mode 1 (after launch_label on
 // the same stream; needs W.rootbits and W.votes).
 // state != nullptr: also the interior state of every site

@@ -22,6 +22,7 @@ HK_ERR_CUDA, HK_ERR_TIMEOUT, HK_ERR_NOMEM = 4, 5, 6
 EXPORTED = ("hk_create", "hk_destroy", "hk_workspace_bytes", "hk_reserve", "hk_label", "hk_label_batched",
             "hk_label_host", "hk_label_host_async", "hk_set_tile", "hk_set_timing", "hk_get_timing", "hk_sync_status", "hk_set_graphs", "hk_last_cuda_error", "hk_strerror", "hk_label_noalloc",
             "hk_noalloc_sync_status", "hk_set_loop_cap", "hk_set_small_path", "hk_set_merge",
+            "hk_label_slab", "hk_slab_faces", "hk_slab_merge",
             "hk_label_interior", "hk_rc_histogram", "hk_interior_state", "hk_interior_update",
             "hk_interior_update_sites",
             "hk_gen_iid", "hk_gen_spheres", "hk_gen_spheres_dev", "hk_gen_capsule")
@@ -70,6 +71,9 @@ def load():
             "hk_set_loop_cap": (I, [P, I64]),
             "hk_set_small_path": (I, [P, I]),
             "hk_set_merge": (I, [P, I, I]),
+            "hk_label_slab": (I, [P, P, I, I, I, I64, I, I, P, P, I64, P, P, P]),
+            "hk_slab_faces": (I, [P, P, I, I, I, P, P, P, I64, P, P, P, P, P]),
+            "hk_slab_merge": (I, [P, I, I, I, I, I, P, P, P, P, I64, P, I, I64, P, P, I64, P, I64, P, P, P]),
             "hk_label_interior": (I, [P, P, I, I, I, P, P, P, I64, P, P, P, P]),
             "hk_rc_histogram": (I, [P, P, I64, P, I, P, P, I, P]),
             "hk_interior_state": (I, [P, P, I, I, I, P, P, P]),
@@ -198,6 +202,27 @@ NOALLOC_SCRATCH_BYTES = 64 << 20
 
 def hk_set_loop_cap(ctx, cap: int) -> int:
     return load().hk_set_loop_cap(ctx, int(cap))
+
+
+def hk_label_slab(ctx, phi, nx, ny, nz, z0, periodic_x, periodic_y, labels_out, sizes_out, sizes_cap, roots_out,
+                  n_clusters_out, stream=0) -> int:
+    return load().hk_label_slab(ctx, phi, nx, ny, nz, int(z0), int(bool(periodic_x)), int(bool(periodic_y)),
+                                labels_out, sizes_out, int(sizes_cap), roots_out, n_clusters_out, stream)
+
+
+def hk_slab_faces(ctx, labels, nx, ny, nz, roots, sizes, n_clusters, sizes_cap, face_out, list_lab_out, list_size_out,
+                  n_face_out, stream=0) -> int:
+    return load().hk_slab_faces(ctx, labels, nx, ny, nz, roots, sizes, n_clusters, int(sizes_cap), face_out,
+                                list_lab_out, list_size_out, n_face_out, stream)
+
+
+def hk_slab_merge(ctx, nranks, rank, periodic_z, nx, ny, face_all, n_face_all, list_lab_all, list_size_all, max_face,
+                  labels, nz, z0, sizes, n_clusters, sizes_cap, own_sizes_out, own_cap, own_n_out, hist_out,
+                  stream=0) -> int:
+    nf = (ctypes.c_int64 * len(n_face_all))(*[int(v) for v in n_face_all])
+    return load().hk_slab_merge(ctx, int(nranks), int(rank), int(bool(periodic_z)), nx, ny, face_all, nf,
+                                list_lab_all, list_size_all, int(max_face), labels, nz, int(z0), sizes, n_clusters,
+                                int(sizes_cap), own_sizes_out, int(own_cap), own_n_out, hist_out, stream)
 
 
 def hk_set_merge(ctx, unions_per_lane: int, combine_hot: int) -> int:
