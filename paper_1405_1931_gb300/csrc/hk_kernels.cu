@@ -859,7 +859,10 @@ __device__ __forceinline__ int site_of(const TileGeo &g, const LatDev &L, int po
     return ((g.z0 + row / TY) * L.ny + (g.y0 + row % TY)) * L.nx + g.x0 + x;
 }
 
-template <int TY, int TZ, int NL>
+// SLAB: one slab of a lattice split along z (W.site_off added to every label, each
+// cluster's label written to W.roots); a separate instance, so that the common path
+// carries neither.
+template <int TY, int TZ, int NL, bool SLAB>
 __global__ void __launch_bounds__(TY * TZ, 1280 / (TY * TZ))
 k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapBatch<NL> TB, Work W, int64_t ntiles) {
     using SH = TileShape<TY, TZ>;
@@ -919,8 +922,7 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapBa
         const int site_row = ((g.z0 + lz) * L.ny + (g.y0 + ly)) * L.nx + g.x0;
         const int site_row0 = (g.z0 * L.ny + g.y0) * L.nx + g.x0, sxy_i = L.nx * L.ny;
         uint32_t rootbits = 0;                // first sites of cluster roots in this row
-        const int soff = (int)W.site_off;     // labels of a slab are sites of the whole lattice
-        const bool want_labels = W.roots != nullptr;
+        const int soff = SLAB ? (int)W.site_off : 0;   // labels of a slab are sites of the whole lattice
         uint32_t w = rs;
         int id = rb;
         while (w) {
@@ -940,12 +942,12 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapBa
             const int crow = ci >> 5;
             const int own = site_row + x0;
             const int other = site_row0 + (crow / TY) * sxy_i + (crow % TY) * L.nx + (ci & 31);
-            const int lab = (isb ? gl : (isr ? own : other)) + soff;
+            const int lab = SLAB ? (isb ? gl : (isr ? own : other)) + soff : (isb ? gl : (isr ? own : other));
             const int size = isr ? (isb ? gs : k) : -1;
             if (size > 0) {
                 if (rank < L.sizes_cap) {
                     L.sizes[rank] = size;
-                    if (want_labels) W.roots[rank] = lab;
+                    if (SLAB) W.roots[rank] = lab;
                 }
                 ++rank;
                 rootbits |= 1u << x0;
@@ -1310,14 +1312,20 @@ static cudaError_t launch_all(const LatDev *lats, int n, const Plan &P, const Wo
             e = cudaFuncSetAttribute(k_tile_label<TY, TZ, NL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem1b);
             if (e != cudaSuccess) return e;
-            e = cudaFuncSetAttribute(k_flatten<TY, TZ, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4);
+            e = cudaFuncSetAttribute(k_flatten<TY, TZ, NL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem4);
             if (e != cudaSuccess) return e;
+            if constexpr (NL == 1) {
+                e = cudaFuncSetAttribute(k_flatten<TY, TZ, NL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem4);
+                if (e != cudaSuccess) return e;
+            }
             e = cudaFuncSetAttribute(k_occupancy_tma<TY, TZ, NL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem0);
             if (e != cudaSuccess) return e;
             c[0] = persistent_grid(k_tile_label<TY, TZ, NL, false>, SH::NT, smem1b, INT32_MAX);
             c[2] = persistent_grid(k_occupancy_tma<TY, TZ, NL>, 256, smem0, INT32_MAX);
-            c[1] = persistent_grid(k_flatten<TY, TZ, NL>, SH::NT, smem4, INT32_MAX);
+            c[1] = persistent_grid(k_flatten<TY, TZ, NL, false>, SH::NT, smem4, INT32_MAX);
         }
         grid1b = c[0];
         grid4 = c[1];
@@ -1353,7 +1361,12 @@ static cudaError_t launch_all(const LatDev *lats, int n, const Plan &P, const Wo
     mark(5);
     k_lattice_finish<NL><<<(unsigned)n, 32, 0, st>>>(B, W);
     mark(6);
-    k_flatten<TY, TZ, NL><<<g4, SH::NT, smem4, st>>>(B, TB, W, P.ntiles);
+    if constexpr (NL == 1) {
+        if (W.roots || W.site_off) k_flatten<TY, TZ, NL, true><<<g4, SH::NT, smem4, st>>>(B, TB, W, P.ntiles);
+        else k_flatten<TY, TZ, NL, false><<<g4, SH::NT, smem4, st>>>(B, TB, W, P.ntiles);
+    } else {
+        k_flatten<TY, TZ, NL, false><<<g4, SH::NT, smem4, st>>>(B, TB, W, P.ntiles);
+    }
     mark(7);
     return cudaGetLastError();
 }
