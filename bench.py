@@ -76,14 +76,15 @@ def dist_env():
 # taken on, identified by TRAFFIC_SOURCE_SHA; after any change to them it is reported
 # as null.
 TRAFFIC_SITES = 512 ** 3
-TRAFFIC_BYTES = {"occupancy": 554.3e6, "tile_label": 63.8e6, "face_merge": 37.2e6, "piece_finalize": 30.0e6,
+TRAFFIC_BYTES = {"occupancy": 554.2e6, "tile_label": 62.0e6, "face_merge": 37.2e6, "piece_finalize": 30.0e6,
                  "scan": 8.5e6, "lattice_finish": 0.0, "flatten": 629.4e6}
-TRAFFIC_SOURCE_SHA = "a269c8563b9c350a"
+TRAFFIC_SOURCE_SHA = "796c37cc6170061d"
 # Warp instructions of one launch of the two instruction-bound passes at 512^3
 # (smsp__inst_executed.sum of one ncu capture of these kernel sources), scaled by
-# sites like the traffic and held to the same kernel sources.  Their roofline is the issue rate: 4 warp
-# schedulers per SM, each issuing at most one warp instruction per clock.
-INST_PER_LAUNCH = {"tile_label": 391975185, "flatten": 195871612}
+# sites like the traffic and held to the same kernel sources.  Their roofline is the
+# issue rate: 4 warp schedulers per SM, each issuing at most one warp instruction per
+# clock.
+INST_PER_LAUNCH = {"tile_label": 362937426, "flatten": 195093372}
 
 
 def kernel_source_sha() -> str:
