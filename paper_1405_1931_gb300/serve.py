@@ -157,7 +157,7 @@ class Server:
                  max_batch_sites: int = 1 << 28, tile: tuple | None = None, graphs: bool = False,
                  producers: int = 4, small_workers: int = 2, small_sites: int = 1 << 21,
                  small_batch_sites: int = 1 << 23, large_backlog: int = 1, small_priority: int = -2,
-                 max_side: int = 512):
+                 large_priority: int = -1, max_side: int = 512):
         import torch
         self.device = device
         self.cap = cap_bytes
@@ -172,7 +172,7 @@ class Server:
         # them, and the small-request workers above the large ones.
         self.producers = [torch.cuda.Stream(device=device) for _ in range(producers)]
         self.streams = ([torch.cuda.Stream(device=device, priority=small_priority) for _ in range(self.n_small)] +
-                        [torch.cuda.Stream(device=device, priority=-1) for _ in range(workers - self.n_small)])
+                        [torch.cuda.Stream(device=device, priority=large_priority) for _ in range(workers - self.n_small)])
         self.labs = [hk.Labeller(device, tile=tile) for _ in range(workers)]
         for lab in self.labs:
             if graphs:
@@ -181,9 +181,15 @@ class Server:
 
     def warm(self, max_side: int):
         """Grow every worker's workspace for the largest request (a cube of max_side) and
-        for a full small batch, and run one small call on each worker, so that no call
-        in service allocates (a cudaMalloc synchronises the device) or sets up kernels."""
+        for a full small batch, run one small call on each worker, and have torch's caching
+        allocator reserve the admission cap once, so that no call or request in service
+        allocates from the driver (a cudaMalloc synchronises the device) or sets up kernels."""
         import torch
+        try:   # fields and outputs are carved from this one cached segment later
+            blk = torch.empty(self.cap, dtype=torch.uint8, device=f"cuda:{self.device}")
+            del blk
+        except RuntimeError:
+            pass
         need = hk.hk_workspace_bytes(max_side, max_side, max_side)
         side = max(1, int(round(self.small_batch_sites ** (1.0 / 3.0))))
         need = max(need, hk.hk_workspace_bytes(side, side, side) * 2)
