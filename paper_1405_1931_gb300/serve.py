@@ -9,11 +9,13 @@ buffers resident on the device and:
 * admits requests while their bytes (field, labels, sizes and the per-lattice
   workspace bound) fit under a memory cap;
 * batches by size: arrived small requests go together into one batched call
-  (``hk_label_batched``) on a free high-priority worker stream, large requests
-  run one per call on the other workers -- each worker owns its own library
-  context, so calls on different workers overlap on the device, and requests
+  (``hk_label_batched``) on a free high-priority worker stream, and requests
   that arrive while others are on the GPU join the next batch as soon as a
-  worker frees up;
+  worker frees up; large requests run one per call, enqueued in arrival order
+  on one large-request stream as soon as they arrive, so that they follow each
+  other on the device with no host round trip between them and none shares the
+  GPU with another large call.  Each worker owns its own library context, so
+  calls on different workers overlap on the device;
 * detects completion with CUDA events and frees the request's memory; once a
   worker's stream is idle it reads that context's device status word, and a
   request whose batch saw a bounded device loop give up is counted as failed.
@@ -145,18 +147,18 @@ class Server:
     only small requests (at most `small_sites` sites), batched together up to
     `max_batch` requests and `small_batch_sites` sites, so that a small request
     never waits behind a large one and its kernels are scheduled ahead of a large
-    call already on the GPU.  The other workers take large requests, oldest
-    first, one per call; while one is running a second starts only when more
-    than `large_backlog` large requests wait (at low load each large request
-    has the GPU to itself, under load they overlap).  They take small batches
-    when no small worker is free and no large request waits.  The FIFO baseline
-    uses one large-request worker.
+    call already on the GPU.  The first of the other workers takes every large
+    request, one per call, in arrival order: it is a queue on its stream, each
+    call enqueued when its request arrives, so that a large request waits only
+    for the large ones before it, as in FIFO, but for none of the small ones.
+    Workers with nothing in flight take small batches when no small worker is
+    free.  The FIFO baseline is every request on the large-request stream.
     """
 
     def __init__(self, device: int = 0, cap_bytes: int = 32 * GB, workers: int = 4, max_batch: int = 64,
                  max_batch_sites: int = 1 << 28, tile: tuple | None = None, graphs: bool = False,
                  producers: int = 4, small_workers: int = 2, small_sites: int = 1 << 21,
-                 small_batch_sites: int = 1 << 23, large_backlog: int = 1, small_priority: int = -2,
+                 small_batch_sites: int = 1 << 23, small_priority: int = -2,
                  large_priority: int = -1, max_side: int = 512):
         import torch
         self.device = device
@@ -165,7 +167,6 @@ class Server:
         self.max_batch_sites = max_batch_sites   # bounds each worker's workspace
         self.small_sites = small_sites
         self.small_batch_sites = small_batch_sites
-        self.large_backlog = large_backlog
         self.n_small = max(0, min(small_workers, workers - 1))
         # Priorities (a lower number is a higher one, clamped to the device's range): the
         # simulation stand-in's producers run at the default, every labelling worker above
@@ -181,9 +182,10 @@ class Server:
 
     def warm(self, max_side: int):
         """Grow every worker's workspace for the largest request (a cube of max_side) and
-        for a full small batch, run one small call on each worker, and have torch's caching
-        allocator reserve the admission cap once, so that no call or request in service
-        allocates from the driver (a cudaMalloc synchronises the device) or sets up kernels."""
+        for a full small batch, run one small call on each worker and each field generator
+        once, and have torch's caching allocator reserve the admission cap once, so that
+        no call or request in service allocates from the driver (a cudaMalloc synchronises
+        the device) or loads kernels."""
         import torch
         try:   # fields and outputs are carved from this one cached segment later
             blk = torch.empty(self.cap, dtype=torch.uint8, device=f"cuda:{self.device}")
@@ -203,6 +205,18 @@ class Server:
                 lab.label_batched([(phi, (1, 1, 1), out), (phi, (0, 1, 0), lab.alloc_outputs(phi.shape, phi.device))],
                                   stream=s)
             lab.sync_status(s)
+        # the stand-in simulation's generators, once each, so that their first launch in
+        # service does not stall the stream behind it
+        side = 64
+        em = Request(-1, 0.0, "emulsion", side, spheres=fields.sphere_params(4, (side, side, side), seed=1))
+        cap = Request(-2, 0.0, "capsule", side, axes=(10.0, 12.0, 14.0))
+        keep = upload_spheres([em])
+        prod = self.producers[0]
+        with torch.cuda.stream(prod):
+            for r in (em, cap):
+                generate(r, prod)
+        prod.synchronize()
+        del keep
 
     def close(self):
         for lab in self.labs:
@@ -228,7 +242,7 @@ class Server:
         # continuous batching uses every worker; the baseline is one launch per
         # request, in arrival order, on a single stream
         fifo = mode == "fifo"
-        free = list(range(len(self.streams)))
+        nbusy = [0] * len(self.streams)          # calls in flight per worker
         used = 0
         peak_used = 0
         done = []
@@ -253,8 +267,7 @@ class Server:
                             r.out = None
                         done.append(r)
                     unchecked[w].extend(batch)
-                    if not fifo:
-                        free.append(w)
+                    nbusy[w] -= 1
                 else:
                     still.append((w, batch, ev))
             inflight = still
@@ -286,14 +299,15 @@ class Server:
             while generated and generated[0].arrival <= now:
                 ready.append(generated.popleft())
             # 4. launches
-            if ready and (free or fifo):
+            if ready:
                 if fifo:
-                    # every request is its own launch, enqueued back to back on one
-                    # large-request worker stream
+                    # every request is its own launch, enqueued back to back on the
+                    # large-request stream
                     w, batch = self.n_small, [ready.popleft()]
                 else:
-                    w, batch = self._pick(ready, free)
+                    w, batch = self._pick(ready, nbusy)
                 if batch:
+                    nbusy[w] += 1
                     s = self.streams[w]
                     for r in batch:
                         s.wait_event(r.gen_event)
@@ -334,47 +348,28 @@ class Server:
             stats["large_p99_ms"] = float(np.percentile(lat[~small], 99))
         return stats
 
-    def _pick(self, ready: deque, free: list):
-        """Continuous mode: the next batch for a free worker, or (-1, []) to wait.
+    def _pick(self, ready: deque, nbusy: list):
+        """Continuous mode: the next batch and its worker, or (-1, []) to wait.
 
-        Small requests go to a free small worker (high priority) as one batch, oldest
-        first, up to max_batch requests and small_batch_sites sites; large requests go
-        to a free large worker one at a time, oldest first; a free large worker with no
-        large request waiting takes a small batch."""
-        small_free = [w for w in free if w < self.n_small]
-        large_free = [w for w in free if w >= self.n_small]
-        has_small = any(r.sites <= self.small_sites for r in ready)
-        has_large = any(r.sites > self.small_sites for r in ready)
-
-        def take_small():
-            batch, sites = [], 0
-            for r in list(ready):
-                if r.sites > self.small_sites:
-                    continue
-                if batch and (len(batch) >= self.max_batch or sites + r.sites > self.small_batch_sites):
-                    break
-                batch.append(r)
-                sites += r.sites
-            for r in batch:
+        The oldest large request goes to the large-request worker whether or not it
+        has calls in flight (its stream keeps them in arrival order); small requests
+        go to a small worker with nothing in flight as one batch, oldest first, up to
+        max_batch requests and small_batch_sites sites, else to another idle worker."""
+        for r in ready:
+            if r.sites > self.small_sites:
                 ready.remove(r)
-            return batch
-
-        if has_small and small_free:
-            w = small_free[0]
-            free.remove(w)
-            return w, take_small()
-        # large requests one at a time while the GPU keeps up (each gets the whole GPU,
-        # as in FIFO); a second and later large worker only when large ones queue up
-        n_large_busy = (len(self.streams) - self.n_small) - len(large_free)
-        n_large_ready = sum(1 for r in ready if r.sites > self.small_sites)
-        if has_large and large_free and (n_large_busy == 0 or n_large_ready > self.large_backlog):
-            w = large_free[0]
-            free.remove(w)
-            r = next(r for r in ready if r.sites > self.small_sites)
+                return self.n_small, [r]
+        idle = [w for w in range(len(self.streams)) if nbusy[w] == 0]
+        if not idle:
+            return -1, []
+        # a small worker, else a spare one, else the large-request worker itself
+        w = min(idle, key=lambda v: (v >= self.n_small, v == self.n_small, v))
+        batch, sites = [], 0
+        for r in list(ready):
+            if batch and (len(batch) >= self.max_batch or sites + r.sites > self.small_batch_sites):
+                break
+            batch.append(r)
+            sites += r.sites
+        for r in batch:
             ready.remove(r)
-            return w, [r]
-        if has_small and large_free and not has_large:
-            w = large_free[0]
-            free.remove(w)
-            return w, take_small()
-        return -1, []
+        return w, batch

@@ -43,3 +43,45 @@ def test_admission_bytes():
     n = r.L ** 3
     assert r.nbytes() == 8 * n + 8 * ((n + 1) // 2) + hk.hk_workspace_bytes(r.L, r.L, r.L)
     assert hk.hk_workspace_bytes(r.L, r.L, r.L) > 0
+
+
+def _sched(n_small=2, workers=4):
+    """A Server with only the scheduling state that `_pick` reads (no device)."""
+    srv = object.__new__(serve.Server)
+    srv.n_small, srv.small_sites, srv.max_batch, srv.small_batch_sites = n_small, 1 << 21, 3, 1 << 23
+    srv.streams = [None] * workers
+    return srv
+
+
+def test_pick_queues_large_requests_on_one_stream_in_arrival_order():
+    from collections import deque
+    srv = _sched()
+    reqs = [serve.Request(k, 0.001 * k, "emulsion", L) for k, L in enumerate([200, 64, 300, 80, 96, 256])]
+    ready = deque(reqs)
+    nbusy = [0, 0, 0, 0]
+    picks = []
+    while ready:
+        w, batch = srv._pick(ready, nbusy)
+        if not batch:
+            break
+        nbusy[w] += 1
+        picks.append((w, [r.rid for r in batch]))
+    # large ones to worker 2 whatever it has in flight, oldest first; the small ones
+    # (<= 128^3) batched, oldest first, on an idle small worker
+    assert [p for p in picks if p[0] == 2] == [(2, [0]), (2, [2]), (2, [5])]
+    assert [p for p in picks if p[0] != 2] == [(0, [1, 3, 4])]
+    assert nbusy == [1, 0, 3, 0]
+
+
+def test_pick_small_batches_wait_for_an_idle_worker():
+    from collections import deque
+    srv = _sched()
+    ready = deque(serve.Request(k, 0.0, "emulsion", 64) for k in range(7))
+    nbusy = [1, 1, 2, 0]
+    w, batch = srv._pick(ready, nbusy)          # both small workers busy: the idle last worker
+    assert w == 3 and [r.rid for r in batch] == [0, 1, 2]   # max_batch 3
+    nbusy[3] = 1
+    assert srv._pick(ready, nbusy) == (-1, [])  # nobody idle: wait
+    nbusy[0] = 0
+    w, batch = srv._pick(ready, nbusy)
+    assert w == 0 and [r.rid for r in batch] == [3, 4, 5]
