@@ -847,8 +847,12 @@ struct FlatSmem {
     using SH = TileShape<TY, TZ>;
     alignas(1024) int32_t stage[SH::SITES];   // labels [lz][ly][x], swizzled (TMA store source)
     static constexpr int GL = SH::MAX_BOUNDARY < 384 ? SH::MAX_BOUNDARY : 384;   // staged boundary pieces
-    int gl[GL];                               // label of each boundary piece's cluster
-    int gsize[GL];                            // cluster size if the piece is the cluster root, else -1
+    static_assert(GL % 4 == 0 && (SH::MAX_BOUNDARY * 4) % 16 == 0 && (SH::MAXRUNS * 2) % 16 == 0,
+                  "bulk copies of whole 16-byte blocks from 16-byte aligned slices");
+    alignas(16) uint16_t codes[SH::MAXRUNS];  // the tile's run codes (bulk copy)
+    alignas(16) int gl[GL];                   // label of each boundary piece's cluster
+    alignas(16) int gsize[GL];                // cluster size if the piece is the cluster root, else -1
+    uint64_t bar;                             // completion of the tile's bulk copies
     int warp_tmp[32];
     int hist[32];
 };
@@ -874,8 +878,18 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapBa
     const bool stage_ok = (smem_u32(S.stage) & 1023u) == 0;
 
     if (tid < 32) S.hist[tid] = 0;
+    if (tid == 0) {
+        mbar_init(&S.bar, 1);
+        fence_mbar_init();
+    }
+    // The tile's run codes and its staged boundary-piece records arrive by bulk copies
+    // issued at the start of the tile, so that the run loop reads shared memory.  If a
+    // copy does not complete within its bound the CTA records STATUS_TMA_TIMEOUT and
+    // reads global memory from then on (prefetch becomes false, uniformly).
+    bool prefetch = true;
+    int ktile = 0;
     int cur_lat = -1;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++ktile) {
         const int lat = (NL == 1) ? 0 : find_lattice(B.lat, B.n, t);
         const LatDev &L = B.lat[lat];
         const TileGeo g = tile_geo<TY, TZ>(L, t);
@@ -895,8 +909,20 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapBa
             pre_lat = W.pre[L.row0];
         }
 
+        const uint16_t *C = W.codes + t * MR;
+        constexpr int GL = FlatSmem<TY, TZ>::GL;
         if (tid == 0) bulk_wait_read0();               // a previous tile's store has read S.stage
-        __syncthreads();
+        __syncthreads();                               // ... and every thread is done with S.codes, S.gl
+        if (prefetch && tid == 0) {
+            const int ncode = (ti.z + 7) & ~7;                       // whole 16-byte blocks
+            const int ng = ((nb < GL ? nb : GL) + 3) & ~3;
+            mbar_arrive_expect_tx(&S.bar, (uint32_t)(2 * ncode + 8 * ng));
+            if (ncode) bulk_load(S.codes, C, 2u * ncode, &S.bar);
+            if (ng) {
+                bulk_load(S.gl, W.key + base, 4u * ng, &S.bar);
+                bulk_load(S.gsize, W.psize + base, 4u * ng, &S.bar);
+            }
+        }
         if (lat != cur_lat) {                          // uniform: flush the histogram per lattice
             if (cur_lat >= 0 && tid < 32 && S.hist[tid] && B.lat[cur_lat].hist)
                 atomicAdd(reinterpret_cast<unsigned long long *>(B.lat[cur_lat].hist) + tid,
@@ -906,15 +932,25 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapBa
             cur_lat = lat;
         }
 
-        const uint16_t *C = W.codes + t * MR;
-        for (int k = tid; k < nb && k < FlatSmem<TY, TZ>::GL; k += NT) {
-            S.gl[k] = __ldg(W.key + base + k);       // cluster label (written by piece_finalize)
-            S.gsize[k] = __ldg(W.psize + base + k);  // cluster size at the root piece, else -1
-        }
         for (int i = tid; i < SH::SITES / 4; i += NT)
             reinterpret_cast<int4 *>(S.stage)[i] = make_int4(-1, -1, -1, -1);
         int tot2;
         const int rb = block_exscan<NT>(__popc(rs), S.warp_tmp, tot2);   // ends with a barrier
+        if (prefetch) {
+            const bool done = mbar_wait_bounded(&S.bar, (uint32_t)(ktile & 1));
+            if (__syncthreads_or(!done)) {             // uniform: give up the prefetch
+                if (tid == 0) atomicOr(W.status, STATUS_TMA_TIMEOUT);
+                mbar_wait_bounded(&S.bar, (uint32_t)(ktile & 1));   // the copies still in flight
+                prefetch = false;
+            }
+        }
+        if (!prefetch) {                               // staged by the threads instead
+            for (int k = tid; k < nb && k < GL; k += NT) {
+                S.gl[k] = __ldg(W.key + base + k);       // cluster label (written by piece_finalize)
+                S.gsize[k] = __ldg(W.psize + base + k);  // cluster size at the root piece, else -1
+            }
+            __syncthreads();
+        }
 
         // a4-a7: one pass over the runs of each row in x order: cluster roots get
         // their rank, size and histogram entry; every run writes its label
@@ -928,7 +964,8 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapBa
         while (w) {
             const int x0 = __ffs(w) - 1;
             w &= w - 1;
-            const int c = __ldg(C + id++);   // a row's codes are consecutive: L1 lines serve them
+            const int c = prefetch ? (int)S.codes[id] : (int)__ldg(C + id);
+            ++id;
             const int k = c & CODE_LOW;
             const bool isb = (c & CODE_BOUNDARY) != 0, isr = (c & CODE_ROOT) != 0;
             const int kk = k < FlatSmem<TY, TZ>::GL ? k : 0;
