@@ -76,15 +76,15 @@ def dist_env():
 # taken on, identified by TRAFFIC_SOURCE_SHA; after any change to them it is reported
 # as null.
 TRAFFIC_SITES = 512 ** 3
-TRAFFIC_BYTES = {"occupancy": 554.2e6, "tile_label": 62.0e6, "face_merge": 37.2e6, "piece_finalize": 30.0e6,
-                 "scan": 8.5e6, "lattice_finish": 0.0, "flatten": 629.4e6}
-TRAFFIC_SOURCE_SHA = "796c37cc6170061d"
+TRAFFIC_BYTES = {"occupancy": 554.3e6, "tile_label": 62.2e6, "face_merge": 37.2e6, "piece_finalize": 30.0e6,
+                 "scan": 8.5e6, "lattice_finish": 0.0, "flatten": 630.9e6}
+TRAFFIC_SOURCE_SHA = "cef50ca87d21031a"
 # Warp instructions of one launch of the two instruction-bound passes at 512^3
 # (smsp__inst_executed.sum of one ncu capture of these kernel sources), scaled by
 # sites like the traffic and held to the same kernel sources.  Their roofline is the
 # issue rate: 4 warp schedulers per SM, each issuing at most one warp instruction per
 # clock.
-INST_PER_LAUNCH = {"tile_label": 362937426, "flatten": 195093372}
+INST_PER_LAUNCH = {"tile_label": 362934388, "flatten": 193646614}
 
 
 def kernel_source_sha() -> str:
@@ -439,6 +439,9 @@ def extra_configs(args, peak):
     # after its request arrives is reported beside it.
     reqs = serve.request_stream(args.served_requests, rate=400.0, seed=3)
     srv = serve.Server(0, cap_bytes=32 * serve.GB, workers=4)
+    # one untimed warm-up run of each mode on another seed, as for every timed form here
+    for mode in ("continuous", "fifo"):
+        srv.serve(serve.request_stream(300, rate=400.0, seed=5), mode=mode)
     cont = srv.serve(reqs)
     reqs = serve.request_stream(args.served_requests, rate=400.0, seed=3)
     fifo = srv.serve(reqs, mode="fifo")
@@ -457,6 +460,7 @@ def extra_configs(args, peak):
         st["roofline_frac"] = (8 * st["sites"] + 256 * st["requests"]) / st["wall_s"] / 1e9 / peak if st["wall_s"] else 0.0
     res["served"] = {"workload": f"{args.served_requests} Poisson requests at 400/s, 80% emulsion / 20% capsule, "
                                  "side log-uniform in [64,512], 32 GB admission cap",
+                     "warmup": "one run of 300 requests (another seed) in each mode first",
                      "continuous": cont, "fifo": fifo,
                      "generated_on_arrival": {"continuous": cont0, "fifo": fifo0},
                      "saturated": {"workload": f"{nsat} requests of the same mix at 20000/s",
