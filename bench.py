@@ -237,13 +237,19 @@ def flush_l2(buf):
 
 
 def time_single(lab, phi, per, reps, flush=None):
-    """Median device time (ms) of hk_label on a resident lattice, L2 flushed between reps."""
+    """Device time (ms, median) of one hk_label call on a resident lattice, L2 flushed
+    between reps when `flush` is given, and the median latency of a call enqueued only
+    once the device is idle (the host's enqueue then counts too).
+
+    For the device time the reps are enqueued back to back (flush, event, call, event),
+    so that the host is ahead of the device and each pair of events brackets the call's
+    kernels and the gaps between them, not the host's work of enqueueing them."""
     import torch
     out = lab.alloc_outputs(phi.shape, phi.device)
     s = torch.cuda.current_stream()
     for _ in range(3):
         lab.label(phi, per, out=out)
-    ts = []
+    evs = []
     for _ in range(reps):
         if flush is not None:
             flush_l2(flush)
@@ -251,10 +257,22 @@ def time_single(lab, phi, per, reps, flush=None):
         a.record(s)
         lab.label(phi, per, out=out)
         b.record(s)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    dev = [a.elapsed_time(b) for a, b in evs]
+    one = []
+    for _ in range(reps):
+        if flush is not None:
+            flush_l2(flush)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        lab.label(phi, per, out=out)
+        b.record(s)
         b.synchronize()
-        ts.append(a.elapsed_time(b))
+        one.append(a.elapsed_time(b))
     lab.sync_status()
-    return float(np.median(ts)), int(out[3].item())
+    return float(np.median(dev)), int(out[3].item()), float(np.median(one))
 
 
 def extra_configs(args, peak):
@@ -266,23 +284,27 @@ def extra_configs(args, peak):
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")   # 256 MB > L2
     lab = hk.Labeller(0)
 
-    def line(name, n_sites, ms, ncl, workload, cache):
+    def line(name, n_sites, ms, ncl, workload, cache, ms_one=None):
         b = 8 * n_sites + 8 * ncl + 256
         res[name] = {"workload": workload, "gsites_per_s": n_sites / (ms * 1e-3) / 1e9, "ms": ms,
-                     "n_clusters": ncl, "roofline_frac": b / (ms * 1e-3) / 1e9 / peak, "cache": cache}
+                     "n_clusters": ncl, "roofline_frac": b / (ms * 1e-3) / 1e9 / peak, "cache": cache,
+                     "timing": "device time, calls enqueued back to back"}
+        if ms_one is not None:   # a call enqueued on an idle device: the host's enqueue included
+            res[name]["ms_one_call_idle_device"] = ms_one
 
     # 32^3, occupancy 0.3, seed 0
     phi = torch.empty((32, 32, 32), dtype=torch.float32, device="cuda")
     hk.hk_gen_iid(phi.data_ptr(), 32, 32, 32, 0, 0.3, hk._stream_handle(None))
-    ms, ncl = time_single(lab, phi, (1, 1, 1), 50, flush)
-    line("small32", 32 ** 3, ms, ncl, "32^3 iid p=0.3 periodic xyz", "L2 flushed between reps")
+    ms, ncl, ms_one = time_single(lab, phi, (1, 1, 1), 50, flush)
+    line("small32", 32 ** 3, ms, ncl, "32^3 iid p=0.3 periodic xyz", "L2 flushed between reps", ms_one)
     # 256^3 emulsion, 600 droplets r in [5, 15]
     L = 256
     phi = torch.empty((L, L, L), dtype=torch.float32, device="cuda")
     c, r = fields.sphere_params(600, (L, L, L), seed=1)
     hk.hk_gen_spheres(phi.data_ptr(), L, L, L, c, r, 8.0, hk._stream_handle(None))
-    ms, ncl = time_single(lab, phi, (1, 1, 1), 20, flush)
-    line("emulsion256", L ** 3, ms, ncl, "256^3 emulsion, 600 droplets r in [5,15], periodic", "L2 flushed between reps")
+    ms, ncl, ms_one = time_single(lab, phi, (1, 1, 1), 20, flush)
+    line("emulsion256", L ** 3, ms, ncl, "256^3 emulsion, 600 droplets r in [5,15], periodic", "L2 flushed between reps",
+         ms_one)
     del phi
 
     # The benchmark of Sec. 3: 1024^3 filled with alternating cubic domains of b^3 sites
@@ -292,7 +314,7 @@ def extra_configs(args, peak):
     sweep = []
     for b in (256, 128, 64, 32, 16, 8, 4, 2, 1):
         phi = fields.block_field_device(L, b)
-        ms, ncl = time_single(lab, phi, (1, 1, 1), 5)
+        ms, ncl, _ = time_single(lab, phi, (1, 1, 1), 5)
         assert ncl == (L // b) ** 3 // 2, (b, ncl)
         sweep.append({"b": b, "n_clusters": ncl, "ms": ms, "gsites_per_s": L ** 3 / (ms * 1e-3) / 1e9})
         del phi
@@ -308,21 +330,28 @@ def extra_configs(args, peak):
     out = lab.alloc_outputs(shape, index.device)
     for _ in range(3):
         res_i = lab.label_interior(index, (1, 1, 1), out=out)
-    ts = []
     s0 = torch.cuda.current_stream()
-    for _ in range(20):
-        flush_l2(flush)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(s0)
-        res_i = lab.label_interior(index, (1, 1, 1), out=out)
-        b.record(s0)
-        b.synchronize()
-        ts.append(a.elapsed_time(b))
-    ms = float(np.median(ts))
+    times = {}
+    for mode in ("back_to_back", "idle_device"):      # as in time_single
+        ts = []
+        for _ in range(20):
+            flush_l2(flush)
+            if mode == "idle_device":
+                torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s0)
+            res_i = lab.label_interior(index, (1, 1, 1), out=out)
+            b.record(s0)
+            ts.append((a, b))
+            if mode == "idle_device":
+                b.synchronize()
+        torch.cuda.synchronize()
+        times[mode] = float(np.median([a.elapsed_time(b) for a, b in ts]))
+    ms = times["back_to_back"]
     ncl = int(res_i[3].item())
     tags = res_i[4][:ncl].cpu().numpy()
     line("capsule_interior256", 256 ** 3, ms, ncl, f"256^3 index field, {len(caps)} capsules (Sec. 6 steps 3-5), periodic",
-         "L2 flushed between reps")
+         "L2 flushed between reps", times["idle_device"])
     res["capsule_interior256"].update({"interior": int((tags == 1).sum()), "exterior": int((tags == 0).sum()),
                                        "undetermined": int((tags == -1).sum())})
     del index, out, res_i

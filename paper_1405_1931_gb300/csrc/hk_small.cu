@@ -96,17 +96,19 @@ __global__ void __launch_bounds__(SNT, 1) k_small_label(const __grid_constant__ 
     const FastDiv div_nbx((uint32_t)nbx), div_ny((uint32_t)ny);
     if (tid < 32) S.hist[tid] = 0;
 
-    // a1: occupancy words; each warp keeps up to 8 segments' loads in flight
-    for (int s0 = wid; s0 < nseg; s0 += NW * 8) {
-        float v[8];
+    // a1: occupancy words; each warp keeps up to 32 segments' loads in flight (a 32^3
+    // lattice in one round trip)
+    constexpr int INF = 32;
+    for (int s0 = wid; s0 < nseg; s0 += NW * INF) {
+        float v[INF];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < INF; ++j) {
             const int s = s0 + NW * j;
             const int q = (int)div_nbx((uint32_t)s), x = (s - q * nbx) * 32 + lane;
             v[j] = (s < nseg && x < nx) ? __ldg(L.phi + (int64_t)q * nx + x) : 0.0f;
         }
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < INF; ++j) {
             const uint32_t w = __ballot_sync(0xffffffffu, occupied(v[j], L.occ_mode));
             if (lane == 0 && s0 + NW * j < nseg) S.m[s0 + NW * j] = w;
         }
@@ -142,9 +144,7 @@ __global__ void __launch_bounds__(SNT, 1) k_small_label(const __grid_constant__ 
     // length 2 repeats an interior edge)
     const int cap = (local_cap > 0 && local_cap < total) ? local_cap : total;
     const int lastbit = (nx - 1) & 31;   // bit of x = nx - 1 in the last segment of a row
-    for (int h = 0; h < 2; ++h) {
-        const int s = 2 * tid + h;
-        if (s >= nseg) break;
+    for (int s = tid; s < nseg; s += SNT) {   // strided: every thread has a segment up to 1024 of them
         const uint32_t w = S.m[s];
         if (!w) continue;
         const int b = S.sb[s];
