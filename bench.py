@@ -15,7 +15,6 @@ scaling); only rank 0 runs the reference arm.
 from __future__ import annotations
 
 import argparse
-import glob
 import hashlib
 import json
 import os
@@ -78,7 +77,7 @@ def dist_env():
 TRAFFIC_SITES = 512 ** 3
 TRAFFIC_BYTES = {"occupancy": 554.3e6, "tile_label": 62.2e6, "face_merge": 37.2e6, "piece_finalize": 30.0e6,
                  "scan": 8.5e6, "lattice_finish": 0.0, "flatten": 630.9e6}
-TRAFFIC_SOURCE_SHA = "cef50ca87d21031a"
+TRAFFIC_SOURCE_SHA = "c2c3e2b3ce10c05c"
 # Warp instructions of one launch of the two instruction-bound passes at 512^3
 # (smsp__inst_executed.sum of one ncu capture of these kernel sources), scaled by
 # sites like the traffic and held to the same kernel sources.  Their roofline is the
@@ -87,10 +86,13 @@ TRAFFIC_SOURCE_SHA = "cef50ca87d21031a"
 INST_PER_LAUNCH = {"tile_label": 362934388, "flatten": 193646614}
 
 
+# the sources of the passes of one hk_label call and of their launch (the captures above
+# measure these kernels; the other sources build other entry points)
+KERNEL_SOURCES = ("hk_kernels.cu", "hk_device.cuh", "hk_launch.h", "hk_api.cu")
+
+
 def kernel_source_sha() -> str:
-    files = []
-    for ext in ("*.cu", "*.cuh", "*.h"):
-        files += glob.glob(os.path.join(ROOT, "paper_1405_1931_gb300", "csrc", ext))
+    files = [os.path.join(ROOT, "paper_1405_1931_gb300", "csrc", f) for f in KERNEL_SOURCES]
     h = hashlib.sha256()
     for f in sorted(files):
         h.update(os.path.basename(f).encode())

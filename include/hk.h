@@ -386,18 +386,23 @@ int hk_set_tile(hk_ctx *ctx, int ty, int tz);
  * Errors: HK_ERR_ARG for other values. */
 int hk_set_merge(hk_ctx *ctx, int unions_per_lane, int combine_hot);
 
-/* The one-launch path for small lattices.  A lattice of at most 32768 sites and
- * 2048 row segments of 32 sites along x (nx rounded up to a multiple of 32, times
- * ny * nz) is labelled by one kernel: one CTA holds the whole lattice in shared
- * memory and runs every step of hk_label there (occupancy, x-runs, their
- * union-find with the periodic edges, ranks, sizes, histogram, labels), so a
- * call is one launch and uses no workspace.  hk_label, hk_label_host(_async)
- * and hk_label_batched take it when every lattice of the call fits (a batch:
- * one CTA per lattice, 64 lattices per launch); results are identical to the
- * tiled passes.  With timing on, such a call reports all its time as the first
- * pass.  enable == 0 makes this context use the tiled passes for every lattice
- * (for tests and comparisons).  Enabled by default.  Drops the context's graphs.
- * Errors: HK_ERR_ARG. */
+/* The one-launch path for small lattices: every step of hk_label (occupancy, x-runs,
+ * their union-find with the periodic edges, ranks, sizes, histogram, labels) in one
+ * kernel, in shared memory, with no workspace.  Two kernels:
+ *   - one CTA holds a lattice of at most 32768 sites and 2048 row segments of 32
+ *     sites along x (nx rounded up to a multiple of 32, times ny * nz);
+ *   - a thread-block cluster of 8 CTAs on 8 SMs holds a lattice whose ny * nz rows,
+ *     cut into 8 equal blocks, come to at most 1024 row segments a block (64^3
+ *     fits); the CTAs reach each other's runs through distributed shared memory.
+ * hk_label, hk_label_host(_async) and hk_label_batched take this path when every
+ * lattice of the call fits: the cluster kernel for calls of at most 16 lattices that
+ * all fit it, else one CTA per lattice where they all fit that; 64 lattices per
+ * launch.  Results are identical to the tiled passes.  With timing on, such a call
+ * reports all its time as the first pass.  enable: 1 (default) as described; 0 this
+ * context uses the tiled passes for every lattice; 2 the one-CTA kernel only; 3 the
+ * cluster kernel only (for tests and comparisons; lattices the chosen kernel cannot
+ * take go to the tiled passes).  Drops the context's graphs.
+ * Errors: HK_ERR_ARG for ctx == NULL or enable outside 0 .. 3. */
 int hk_set_small_path(hk_ctx *ctx, int enable);
 
 /* Per-pass timing.  hk_set_timing(ctx, 1) resets the totals and makes every

@@ -61,7 +61,7 @@ struct hk_ctx {
     int32_t *dstatus = nullptr;   // device status word (STATUS_* flags), survives workspace growth
     int64_t loop_cap = 0;         // test bound of the capped union-find loops (0: natural bounds)
     int64_t *dcounts = nullptr;   // device cluster counts of the one-CTA path when the caller gives none
-    bool small_path = true;       // lattices that fit take the one-CTA path
+    int small_path = 1;           // one-launch kernels: 0 off, 1 the library picks, 2 one CTA only, 3 cluster only
     hk::MergeSchedule merge;      // unions per lane of the face merge, hot-root combining
     void *slab_fmap = nullptr;    // face-cluster number of each local cluster (hk_slab_faces -> hk_slab_merge)
     size_t slab_fmap_bytes = 0;
@@ -88,6 +88,9 @@ struct hk_ctx {
 namespace {
 
 constexpr int DEFAULT_TY = 16, DEFAULT_TZ = 16;
+// calls of at most this many small lattices take the cluster kernel (8 SMs each; more
+// lattices than the device holds clusters at once go one CTA each)
+constexpr int CLUSTER_MAX_LATTICES = 16;
 constexpr int64_t MAX_SITES = (int64_t)1 << 31;
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -236,7 +239,7 @@ int ensure_status(hk_ctx *ctx) {
 // Lattices that all fit the one-CTA path (hk::small_fits), n <= MAX_LAT_PER_LAUNCH: one
 // launch, no workspace.  Same capacity rule and outputs as the tiled path; with timing on,
 // the whole launch counts as the first pass.
-int run_small(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st, bool check_capacity) {
+int run_small(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st, bool check_capacity, bool cluster) {
     int rc = ensure_status(ctx);
     if (rc != HK_OK) return rc;
     if (!ctx->dcounts) {
@@ -270,7 +273,7 @@ int run_small(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st, bool 
         cudaEventRecord(ev[0], st);
     }
     const int32_t lcap = (ctx->loop_cap > 0 && ctx->loop_cap < INT32_MAX) ? (int32_t)ctx->loop_cap : 0;
-    cudaError_t e = hk::launch_small(dev.data(), n, ctx->dstatus, lcap, st);
+    cudaError_t e = hk::launch_small(dev.data(), n, ctx->dstatus, lcap, st, cluster);
     if (e != cudaSuccess) return fail_cuda(ctx, e);
     if (ev)
         for (int i = 1; i <= hk::NUM_PASSES; ++i) cudaEventRecord(ev[i], st);
@@ -305,14 +308,22 @@ int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st, bo
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return fail_cuda(ctx, e);
 
-    // small lattices: one CTA each, up to MAX_LAT_PER_LAUNCH per launch
+    // Small lattices take one launch: a thread-block cluster of 8 CTAs per lattice for
+    // calls of a few lattices (latency: the work of a lattice spread over 8 SMs), one
+    // CTA per lattice for larger batches of lattices that fit it (throughput); up to
+    // MAX_LAT_PER_LAUNCH lattices per launch.
     if (!index_field && ctx->small_path && !roots && site_off == 0) {
-        bool all_small = true;
-        for (int i = 0; i < n && all_small; ++i) all_small = hk::small_fits(lats[i].nx, lats[i].ny, lats[i].nz);
-        if (all_small) {
+        bool all_one = ctx->small_path != 3, all_cluster = ctx->small_path != 2 && hk::cluster_ok();
+        for (int i = 0; i < n && (all_one || all_cluster); ++i) {
+            all_one = all_one && hk::small_fits(lats[i].nx, lats[i].ny, lats[i].nz);
+            all_cluster = all_cluster && hk::cluster_fits(lats[i].nx, lats[i].ny, lats[i].nz);
+        }
+        if (all_one || all_cluster) {
+            const bool cluster = all_cluster && (!all_one || n <= CLUSTER_MAX_LATTICES);
             int rc_cap = HK_OK;
             for (int c0 = 0; c0 < n; c0 += hk::MAX_LAT_PER_LAUNCH) {
-                const int rc = run_small(ctx, lats + c0, std::min(n - c0, hk::MAX_LAT_PER_LAUNCH), st, check_capacity);
+                const int rc = run_small(ctx, lats + c0, std::min(n - c0, hk::MAX_LAT_PER_LAUNCH), st, check_capacity,
+                                         cluster);
                 if (rc == HK_ERR_CAPACITY) rc_cap = rc;
                 else if (rc != HK_OK) return rc;
             }
@@ -795,8 +806,8 @@ int hk_set_merge(hk_ctx *ctx, int unions_per_lane, int combine_hot) {
 }
 
 int hk_set_small_path(hk_ctx *ctx, int enable) {
-    if (!ctx) return HK_ERR_ARG;
-    ctx->small_path = enable != 0;
+    if (!ctx || enable < 0 || enable > 3) return HK_ERR_ARG;
+    ctx->small_path = enable;
     drop_graphs(ctx);
     return HK_OK;
 }

@@ -16,6 +16,8 @@
 // Runs are numbered in row-major order of their first sites, so each cluster's root
 // (its smallest run id) holds its smallest site, and ranking roots by run id ranks the
 // clusters by label.  No workspace is used: the results go straight to the outputs.
+#include <cooperative_groups.h>
+
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -53,9 +55,12 @@ struct FastDiv {
 // the run of segment s (first run id b, occupancy word w) holding bit x
 __device__ __forceinline__ int srun(int b, uint32_t w, int x) { return b + __popc(run_starts(w) & le_mask(x)) - 1; }
 
-// Exclusive scan of one int per thread over the CTA's 1024 threads; *total gets the sum.
-// Ends with a barrier, after which warp_tmp and scan_total may be reused.
-__device__ __forceinline__ int cta_exscan(int v, SmallSmem &S, int &total) {
+// Exclusive scan of one int per thread over the CTA's NT threads (NT a multiple of 32,
+// at most 1024); *total gets the sum.  Ends with a barrier, after which warp_tmp and
+// scan_total may be reused.
+template <int NT, class SM>
+__device__ __forceinline__ int cta_exscan(int v, SM &S, int &total) {
+    constexpr int NW = NT / 32;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int inc = v;
 #pragma unroll
@@ -66,14 +71,14 @@ __device__ __forceinline__ int cta_exscan(int v, SmallSmem &S, int &total) {
     if (lane == 31) S.warp_tmp[wid] = inc;
     __syncthreads();
     if (wid == 0) {
-        const int w = S.warp_tmp[lane];
+        const int w = lane < NW ? S.warp_tmp[lane] : 0;
         int wi = w;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const int u = __shfl_up_sync(0xffffffffu, wi, d);
             if (lane >= d) wi += u;
         }
-        S.warp_tmp[lane] = wi - w;
+        if (lane < NW) S.warp_tmp[lane] = wi - w;
         if (lane == 31) S.scan_total = wi;
     }
     __syncthreads();
@@ -120,7 +125,7 @@ __global__ void __launch_bounds__(SNT, 1) k_small_label(const __grid_constant__ 
     const int n_a = s_a < nseg ? __popc(run_starts(S.m[s_a])) : 0;
     const int n_b = s_b < nseg ? __popc(run_starts(S.m[s_b])) : 0;
     int total;
-    const int base = cta_exscan(n_a + n_b, S, total);
+    const int base = cta_exscan<SNT>(n_a + n_b, S, total);
     if (s_a < nseg) S.sb[s_a] = (uint16_t)base;
     if (s_b < nseg) S.sb[s_b] = (uint16_t)(base + n_a);
     for (int h = 0; h < 2; ++h) {   // own node and descriptor of every run
@@ -188,7 +193,7 @@ __global__ void __launch_bounds__(SNT, 1) k_small_label(const __grid_constant__ 
     int nr = 0;
     for (int i = i0; i < i1; ++i) nr += S.par[i] == i;
     int nclus;
-    int rank = cta_exscan(nr, S, nclus);
+    int rank = cta_exscan<SNT>(nr, S, nclus);
     const int64_t capr = L.sizes_cap;
     for (int i = i0; i < i1; ++i) {
         if (S.par[i] != i) continue;
@@ -214,6 +219,346 @@ __global__ void __launch_bounds__(SNT, 1) k_small_label(const __grid_constant__ 
     if (tid == 0 && L.ncl) L.ncl[0] = nclus;
 }
 
+// ---------------------------------------------------------------------------------------
+// The same steps on a thread-block cluster: CS CTAs on CS SMs label one lattice, each
+// holding the rows [c RP, (c + 1) RP) of the lattice (RP = ceil(ny nz / CS)) in its own
+// shared memory, so that the loads, unions, ranks and label stores are spread over CS
+// SMs.  A run of CTA c is numbered (c << CRUN_BITS) | its local id: numbers grow with
+// the runs' first sites in row-major order, so union by minimum number still makes each
+// cluster's root its first run.  Each CTA first joins the edges inside it on local ids;
+// the edges to other CTAs are then joined between local roots, through distributed
+// shared memory (the other CTAs' parents, occupancy words and run bases); every local
+// root then learns its cluster root, so each run reaches its root in two steps, and
+// each run's label is resolved once per run, not per site.  The phases that reach other
+// CTAs are separated by cluster barriers.
+// ---------------------------------------------------------------------------------------
+constexpr int CS = 8;              // CTAs per lattice (a portable cluster size)
+constexpr int CNT = 512;           // threads per CTA
+constexpr int CSEG = 1024;         // row segments per CTA
+constexpr int CRUN_BITS = 14;
+constexpr int CRUN = 1 << CRUN_BITS;   // runs per CTA: at most 16 per segment
+constexpr int DESC_LROOT = 0x8000;     // desc flag: the run is the root of its CTA-local tree
+static_assert(16 * CSEG <= CRUN && CSEG <= 2 * CNT, "run ids of a CTA; two segments per thread in the scan");
+
+struct ClusterSmem {
+    uint32_t m[CSEG];        // occupancy word of each of this CTA's row segments
+    uint16_t sb[CSEG];       // first local run id of each segment
+    int par[CRUN];           // union-find over cluster run numbers; after compression: the root
+    int sz[CRUN];            // piece size, summed at each root; after ranking: the root's site
+    uint16_t desc[CRUN];     // per run: (local segment << 5) | first x, and DESC_LROOT
+    int roots;               // cluster roots among this CTA's runs
+    int warp_tmp[32];
+    int scan_total;
+    int hist[32];
+};
+static_assert(sizeof(ClusterSmem) <= 227 * 1024, "one CTA's shared memory");
+
+namespace cg = cooperative_groups;
+
+struct ClusterView {
+    ClusterSmem &S;
+    cg::cluster_group cl;
+    int c;
+    // parent of run number g, wherever it lives
+    __device__ __forceinline__ int *par(int g) const {
+        int *p = &S.par[g & (CRUN - 1)];
+        const int o = g >> CRUN_BITS;
+        return o == c ? p : cl.map_shared_rank(p, o);
+    }
+    __device__ __forceinline__ int *sz(int g) const {
+        int *p = &S.sz[g & (CRUN - 1)];
+        const int o = g >> CRUN_BITS;
+        return o == c ? p : cl.map_shared_rank(p, o);
+    }
+    // find with path halving (every store lowers a parent to an ancestor)
+    __device__ int find(int x) const {
+        int p = *par(x);
+        while (p != x) {
+            const int gp = *par(p);
+            if (gp == p) return p;
+            *par(x) = gp;
+            x = gp;
+            p = *par(x);
+        }
+        return x;
+    }
+    __device__ int find_ro(int x) const {
+        int p = *par(x);
+        while (p != x) {
+            x = p;
+            p = *par(x);
+        }
+        return x;
+    }
+    // each retry strictly lowers max(a, b): at most `cap` rounds
+    __device__ void unite(int a, int b, int cap, int32_t *status) const {
+        for (int it = 0; it <= cap; ++it) {
+            a = find(a);
+            b = find(b);
+            if (a == b) return;
+            const int hi = a > b ? a : b, lo = a > b ? b : a;
+            const int old = atomicMin(par(hi), lo);
+            if (old == hi) return;
+            a = lo;
+            b = old;
+        }
+        atomicOr(status, STATUS_LOCAL_LOOP);
+    }
+};
+
+template <int NL>
+__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(CNT, 1)
+    k_small_cluster(const __grid_constant__ LatBatch<NL> B, int32_t *status, int32_t local_cap) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ClusterSmem &S = *reinterpret_cast<ClusterSmem *>(smem_raw);
+    cg::cluster_group cl = cg::this_cluster();
+    const int c = (int)cl.block_rank();
+    const ClusterView V{S, cl, c};
+    const LatDev &L = B.lat[blockIdx.x / CS];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    constexpr int NW = CNT / 32;
+    const int nx = L.nx, ny = L.ny, nz = L.nz, nbx = L.nbx;
+    const int nrows = ny * nz, rp = (nrows + CS - 1) / CS;       // rows per CTA
+    const int q0 = min(c * rp, nrows), q1 = min(q0 + rp, nrows);
+    const int seg0 = q0 * nbx, nseg = (q1 - q0) * nbx;           // this CTA's segments
+    const FastDiv div_nbx((uint32_t)nbx), div_ny((uint32_t)ny), div_rp((uint32_t)rp);
+    const int cbase = c << CRUN_BITS;
+    if (tid < 32) S.hist[tid] = 0;
+
+    // a1: occupancy words of this CTA's segments, 32 loads in flight per warp
+    constexpr int INF = 32;
+    for (int l0 = wid; l0 < nseg; l0 += NW * INF) {
+        float v[INF];
+#pragma unroll
+        for (int j = 0; j < INF; ++j) {
+            const int ls = l0 + NW * j, sg = seg0 + ls;
+            const int q = (int)div_nbx((uint32_t)sg), x = (sg - q * nbx) * 32 + lane;
+            v[j] = (ls < nseg && x < nx) ? __ldg(L.phi + (int64_t)q * nx + x) : 0.0f;
+        }
+#pragma unroll
+        for (int j = 0; j < INF; ++j) {
+            const uint32_t w = __ballot_sync(0xffffffffu, occupied(v[j], L.occ_mode));
+            if (lane == 0 && l0 + NW * j < nseg) S.m[l0 + NW * j] = w;
+        }
+    }
+    __syncthreads();
+
+    // a2: local run ids (segments 2t and 2t + 1 of thread t), nodes and descriptors
+    const int s_a = 2 * tid, s_b = 2 * tid + 1;
+    const int n_a = s_a < nseg ? __popc(run_starts(S.m[s_a])) : 0;
+    const int n_b = s_b < nseg ? __popc(run_starts(S.m[s_b])) : 0;
+    int total;
+    const int base = cta_exscan<CNT>(n_a + n_b, S, total);
+    if (s_a < nseg) S.sb[s_a] = (uint16_t)base;
+    if (s_b < nseg) S.sb[s_b] = (uint16_t)(base + n_a);
+    for (int h = 0; h < 2; ++h) {
+        const int ls = 2 * tid + h;
+        if (ls >= nseg) break;
+        uint32_t w = run_starts(S.m[ls]);
+        int id = base + (h ? n_a : 0);
+        while (w) {
+            const int x0 = __ffs(w) - 1;
+            w &= w - 1;
+            S.par[id] = id;   // local ids until the edges inside this CTA are joined
+            S.desc[id] = (uint16_t)((ls << 5) | x0);
+            ++id;
+        }
+    }
+    __syncthreads();
+
+    // a3: unions with the lower neighbours along x, y and z and across the periodic
+    // edges, in two rounds.  First the edges inside this CTA, on local run ids in its own
+    // shared memory; then, once every CTA has compressed its runs onto their local roots,
+    // the edges to runs of other CTAs, joined between local roots through distributed
+    // shared memory.  Each round lists its run pairs first (a scan of per-segment counts;
+    // sz serves as the list), so that the unions spread over all threads; a round whose
+    // list would not fit joins each segment's pairs where they are found.
+    const int lastbit = (nx - 1) & 31;
+    auto neighbours = [&](int ls, auto &&edge) {   // edge(global segment t) for every lower neighbour
+        const int sg = seg0 + ls;
+        const int q = (int)div_nbx((uint32_t)sg), z = (int)div_ny((uint32_t)q), y = q - z * ny;
+        if (y > 0) edge(sg - nbx);
+        else if (L.per[1] && ny >= 2) edge(sg + (ny - 1) * nbx);
+        if (z > 0) edge(sg - nbx * ny);
+        else if (L.per[2] && nz >= 2) edge(sg + (nz - 1) * nbx * ny);
+    };
+    auto owner = [&](int t, int &lt) {   // the CTA holding global segment t, and its local index there
+        const int tq = (int)div_nbx((uint32_t)t), o = (int)div_rp((uint32_t)tq);
+        lt = t - o * rp * nbx;
+        return o;
+    };
+    // every pair of runs joined by an edge of segment ls: pair(own local run, CTA, its run)
+    auto pairs = [&](int ls, bool cross, auto &&pair) {
+        const uint32_t w = S.m[ls];
+        if (!w) return;
+        const int b = S.sb[ls];
+        neighbours(ls, [&](int t) {
+            int lt;
+            const int o = owner(t, lt);
+            if ((o != c) != cross) return;
+            const uint32_t wt = o == c ? S.m[lt] : *cl.map_shared_rank(&S.m[lt], o);
+            uint32_t os = run_starts(w & wt);
+            if (!os) return;
+            const int bt = o == c ? S.sb[lt] : *cl.map_shared_rank(&S.sb[lt], o);
+            while (os) {
+                const int x = __ffs(os) - 1;
+                os &= os - 1;
+                pair(srun(b, w, x), o, srun(bt, wt, x));
+            }
+        });
+        if (cross) return;
+        const int bx = (seg0 + ls) - (int)div_nbx((uint32_t)(seg0 + ls)) * nbx;   // a row lives in one CTA
+        if ((w & 1u) && bx > 0 && (S.m[ls - 1] >> 31)) pair(b, c, srun(S.sb[ls - 1], S.m[ls - 1], 31));
+        if ((w & 1u) && bx == 0 && L.per[0] && nx >= 2) {
+            const int t = ls + nbx - 1;
+            if ((S.m[t] >> lastbit) & 1u) pair(b, c, srun(S.sb[t], S.m[t], lastbit));
+        }
+    };
+    // one round: count, list and join the pairs of this thread's segments (2t, 2t + 1)
+    auto round = [&](bool cross, auto &&join) {
+        int np = 0;
+        for (int h = 0; h < 2; ++h)
+            if (2 * tid + h < nseg) pairs(2 * tid + h, cross, [&](int, int, int) { ++np; });
+        int npairs;
+        int j = cta_exscan<CNT>(np, S, npairs);
+        if (npairs <= CRUN) {
+            for (int h = 0; h < 2; ++h)
+                if (2 * tid + h < nseg)
+                    pairs(2 * tid + h, cross, [&](int a, int o, int bb) {
+                        S.sz[j++] = (a << (CRUN_BITS + 3)) | (o << CRUN_BITS) | bb;
+                    });
+            __syncthreads();
+            for (int k = tid; k < npairs; k += CNT) {
+                const int v = S.sz[k];
+                join(v >> (CRUN_BITS + 3), (v >> CRUN_BITS) & 7, v & (CRUN - 1));
+            }
+        } else {
+            for (int h = 0; h < 2; ++h)
+                if (2 * tid + h < nseg) pairs(2 * tid + h, cross, join);
+        }
+    };
+    static_assert(CS <= 8 && 2 * CRUN_BITS + 3 <= 31, "a listed pair packs into one int");
+    {
+        const int lcap = (local_cap > 0 && local_cap < total) ? local_cap : total;
+        round(false, [&](int a, int, int bb) { s_union(S.par, a, bb, lcap, status); });
+        __syncthreads();
+        // local roots, then cluster numbers: every run points at its local root
+        for (int i = tid; i < total; i += CNT) S.sz[i] = s_find_ro(S.par, i);
+        __syncthreads();
+        for (int i = tid; i < total; i += CNT) {
+            const int r = S.sz[i];
+            S.par[i] = cbase | r;
+            if (r == i) S.desc[i] |= DESC_LROOT;
+        }
+    }
+    cl.sync();
+    {   // the edges to other CTAs, joined between the two runs' local roots
+        const int cap = (local_cap > 0 && local_cap < CS * CRUN) ? local_cap : CS * CRUN;
+        round(true, [&](int a, int o, int bb) {
+            V.unite(S.par[a], *cl.map_shared_rank(&S.par[bb], o), cap, status);
+        });
+    }
+    __syncthreads();                                  // the pair list is read
+    for (int i = tid; i < total; i += CNT) S.sz[i] = 0;
+    cl.sync();                                        // ... and every size slot cleared
+    // every local root learns its cluster's root (the finds that cross CTAs walk only
+    // local roots); the other runs still point at their local roots
+    for (int i = tid; i < total; i += CNT)
+        if (S.desc[i] & DESC_LROOT) S.par[i] = V.find_ro(cbase | i);
+    __syncthreads();
+
+    // compression and piece sizes: a run's cluster root is its local root's (two reads
+    // of this CTA's shared memory); the run lengths of a group of lanes with the same
+    // root are added once, at the root's CTA
+    for (int i0 = 0; i0 < total; i0 += CNT) {   // warp-uniform trips
+        const int i = i0 + tid;
+        int root = -1, len = 0;
+        if (i < total) {
+            const int d = S.desc[i];
+            root = (d & DESC_LROOT) ? S.par[i] : S.par[S.par[i] & (CRUN - 1)];
+            len = run_len(S.m[(d & ~DESC_LROOT) >> 5], d & 31);
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, root);
+        const int sum = (int)__reduce_add_sync(peers, (unsigned)len);
+        if (root >= 0 && lane == __ffs(peers) - 1) atomicAdd(V.sz(root), sum);
+    }
+    __syncthreads();
+    for (int i = tid; i < total; i += CNT)   // every run now points at its cluster root
+        if (!(S.desc[i] & DESC_LROOT)) S.par[i] = S.par[S.par[i] & (CRUN - 1)];
+    cl.sync();
+
+    // a4, a6, a7: the roots in run order get consecutive ranks; the roots of the CTAs
+    // before this one come first
+    const int per = (total + CNT - 1) / CNT;
+    const int i0 = tid * per, i1 = min(i0 + per, total);
+    int nr = 0;
+    for (int i = i0; i < i1; ++i) nr += S.par[i] == (cbase | i);
+    int nroots;
+    int rank = cta_exscan<CNT>(nr, S, nroots);
+    if (tid == 0) S.roots = nroots;
+    cl.sync();
+    int all = 0;
+    if (wid == 0) {
+        const int r = lane < CS ? (lane == c ? nroots : *cl.map_shared_rank(&S.roots, lane)) : 0;
+        const int before = (int)__reduce_add_sync(0xffffffffu, (unsigned)(lane < c ? r : 0));
+        all = (int)__reduce_add_sync(0xffffffffu, (unsigned)r);
+        if (lane == 0) S.scan_total = before;
+    }
+    __syncthreads();
+    rank += S.scan_total;
+    const int64_t capr = L.sizes_cap;
+    for (int i = i0; i < i1; ++i) {
+        if (S.par[i] != (cbase | i)) continue;
+        const int size = S.sz[i];
+        if (rank < capr) L.sizes[rank] = size;
+        ++rank;
+        atomicAdd(&S.hist[31 - __clz(size)], 1);
+    }
+    __syncthreads();   // this CTA's sizes are out: sz now takes each run's label
+
+    // each run's label, the first site of its cluster's root run (the root's descriptor,
+    // read once per group of lanes with the same root)
+    for (int i0 = 0; i0 < total; i0 += CNT) {
+        const int i = i0 + tid;
+        const int root = i < total ? S.par[i] : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, root);
+        const int leader = __ffs(peers) - 1;
+        int d = 0;
+        if (root >= 0 && lane == leader) {
+            const int o = root >> CRUN_BITS;
+            const uint16_t *dp = &S.desc[root & (CRUN - 1)];
+            d = o == c ? *dp : *cl.map_shared_rank(dp, o);
+        }
+        d = __shfl_sync(0xffffffffu, d, leader) & ~DESC_LROOT;
+        if (i < total) {
+            const int sg = (root >> CRUN_BITS) * rp * nbx + (d >> 5), rq = (int)div_nbx((uint32_t)sg);
+            S.sz[i] = rq * nx + (sg - rq * nbx) * 32 + (d & 31);
+        }
+    }
+    __syncthreads();
+
+    // a5: labels, one warp per segment, one lane per site, four segments a step
+    for (int l0 = wid; l0 < nseg; l0 += 4 * NW) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int ls = l0 + u * NW;
+            if (ls >= nseg) break;
+            const int sg = seg0 + ls;
+            const int q = (int)div_nbx((uint32_t)sg), x = (sg - q * nbx) * 32 + lane;
+            const uint32_t w = S.m[ls];
+            const int lab = ((w >> lane) & 1u) ? S.sz[srun(S.sb[ls], w, lane)] : -1;
+            if (x < nx) L.labels[(int64_t)q * nx + x] = lab;
+        }
+    }
+    // the histogram of the whole lattice gathers in CTA 0
+    if (c != 0 && tid < 32 && S.hist[tid]) atomicAdd(cl.map_shared_rank(&S.hist[tid], 0), S.hist[tid]);
+    cl.sync();   // no CTA's shared memory is reached after this
+    if (c == 0) {
+        if (tid < 32 && L.hist) L.hist[tid] = S.hist[tid];
+        if (tid == 0 && L.ncl) L.ncl[0] = all;
+    }
+}
+
 }  // namespace
 
 bool small_fits(int nx, int ny, int nz) {
@@ -222,12 +567,71 @@ bool small_fits(int nx, int ny, int nz) {
     return N <= SMALL_MAX_SITES && nseg <= SMALL_MAX_SEG;
 }
 
-cudaError_t launch_small(const LatDev *lats, int n, int32_t *status, int32_t local_cap, cudaStream_t st) {
+bool cluster_fits(int nx, int ny, int nz) {
+    const int64_t nbx = (nx + TX - 1) / TX, rows = (int64_t)ny * nz;
+    return nx >= 1 && ny >= 1 && nz >= 1 && ((rows + CS - 1) / CS) * nbx <= CSEG;
+}
+
+bool cluster_ok() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
+        cudaGetLastError();
+        return false;
+    }
+    static int state[MAX_DEVICES];   // 0 unknown, 1 the cluster kernel can run, 2 it cannot
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!state[dev]) {
+        bool ok = cudaFuncSetAttribute(k_small_cluster<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(ClusterSmem)) == cudaSuccess &&
+                  cudaFuncSetAttribute(k_small_cluster<MAX_LAT_PER_LAUNCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(ClusterSmem)) == cudaSuccess;
+        if (ok) {   // at least one cluster of CS CTAs with this much shared memory fits the device
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(CS, 1, 1);
+            cfg.blockDim = dim3(CNT, 1, 1);
+            cfg.dynamicSmemBytes = sizeof(ClusterSmem);
+            cudaLaunchAttribute attr;
+            attr.id = cudaLaunchAttributeClusterDimension;
+            attr.val.clusterDim.x = CS;
+            attr.val.clusterDim.y = 1;
+            attr.val.clusterDim.z = 1;
+            cfg.attrs = &attr;
+            cfg.numAttrs = 1;
+            int nclusters = 0;
+            ok = cudaOccupancyMaxActiveClusters(&nclusters, k_small_cluster<1>, &cfg) == cudaSuccess && nclusters > 0;
+        }
+        if (!ok) cudaGetLastError();
+        state[dev] = ok ? 1 : 2;
+    }
+    return state[dev] == 1;
+}
+
+cudaError_t launch_small(const LatDev *lats, int n, int32_t *status, int32_t local_cap, cudaStream_t st,
+                         bool cluster) {
     if (n <= 0) return cudaSuccess;
+    if (n > MAX_LAT_PER_LAUNCH) return cudaErrorInvalidValue;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+    if (cluster) {   // cluster_ok() has set the kernels' shared-memory attribute
+        if (n == 1) {
+            LatBatch<1> B;
+            std::memset(&B, 0, sizeof(B));
+            B.n = 1;
+            B.lat[0] = lats[0];
+            k_small_cluster<1><<<CS, CNT, sizeof(ClusterSmem), st>>>(B, status, local_cap);
+        } else {
+            LatBatch<MAX_LAT_PER_LAUNCH> B;
+            std::memset(&B, 0, sizeof(B));
+            B.n = n;
+            for (int i = 0; i < n; ++i) B.lat[i] = lats[i];
+            k_small_cluster<MAX_LAT_PER_LAUNCH><<<(unsigned)(CS * n), CNT, sizeof(ClusterSmem), st>>>(B, status,
+                                                                                                      local_cap);
+        }
+        return cudaGetLastError();
+    }
     static bool attr_set[MAX_DEVICES][2];
     static std::mutex mu;
     std::lock_guard<std::mutex> lock(mu);
@@ -243,7 +647,6 @@ cudaError_t launch_small(const LatDev *lats, int n, int32_t *status, int32_t loc
         B.lat[0] = lats[0];
         k_small_label<1><<<1, SNT, sizeof(SmallSmem), st>>>(B, status, local_cap);
     } else {
-        if (n > MAX_LAT_PER_LAUNCH) return cudaErrorInvalidValue;
         if (!attr_set[dev][1]) {
             e = cudaFuncSetAttribute(k_small_label<MAX_LAT_PER_LAUNCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)sizeof(SmallSmem));

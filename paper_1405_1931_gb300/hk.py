@@ -230,7 +230,7 @@ def hk_set_merge(ctx, unions_per_lane: int, combine_hot: int) -> int:
 
 
 def hk_set_small_path(ctx, enable: bool) -> int:
-    return load().hk_set_small_path(ctx, int(bool(enable)))
+    return load().hk_set_small_path(ctx, int(enable))
 
 
 def hk_set_tile(ctx, ty, tz) -> int:
@@ -342,9 +342,10 @@ class Labeller:
             raise HKError(rc, "hk_set_merge")
         self.merge = (unions_per_lane or 2, combine_hot)
 
-    def set_small_path(self, enable: bool = True):
-        """Let lattices that fit take the one-CTA path (default), or force the tiled passes."""
-        rc = hk_set_small_path(self.ctx, enable)
+    def set_small_path(self, enable=True):
+        """One-launch kernels for small lattices: True/1 the library picks (default), False/0
+        the tiled passes always, 2 the one-CTA kernel only, 3 the cluster kernel only."""
+        rc = hk_set_small_path(self.ctx, int(enable))
         if rc != HK_OK:
             raise HKError(rc, "hk_set_small_path")
 

@@ -1,11 +1,14 @@
 """The one-launch path for small lattices against the oracle, element by element.
 
-A lattice of at most 32768 sites and 2048 row segments is labelled by one CTA in
-shared memory (hk_small.cu).  Labels, sizes, histogram and count must equal the
-oracle's exactly on every shape and periodic set it takes: axes of length 1 and
-2, ragged x, both size limits, the site checkerboard with its V/2 clusters at the
-limit, empty and full lattices, and batches of more lattices than one launch
-holds.  A lattice just beyond the limit takes the tiled passes, also checked.
+Two kernels (hk_small.cu): one CTA holds a lattice of at most 32768 sites and 2048
+row segments in shared memory; a cluster of 8 CTAs holds a lattice whose rows, cut
+into 8 blocks, come to at most 1024 row segments a block, the CTAs reaching each
+other's runs through distributed shared memory.  Under each kernel alone, labels,
+sizes, histogram and count must equal the oracle's exactly on every shape and
+periodic set it takes: axes of length 1 and 2, ragged x, the size limits, the site
+checkerboard with its V/2 clusters at the limit, empty and full lattices, and
+batches of more lattices than one launch holds.  Lattices just beyond a limit take
+the tiled passes, also checked.
 """
 import itertools
 
@@ -21,10 +24,21 @@ pytestmark = pytest.mark.gpu
 PERIODIC_ALL = list(itertools.product((0, 1), repeat=3))
 
 
-@pytest.fixture(scope="module")
-def labeller():
+@pytest.fixture(scope="module", params=[("one_cta", 2), ("cluster", 3)], ids=lambda p: p[0])
+def labeller(request):
+    """A context whose small path uses one kernel only."""
     from paper_1405_1931_gb300.hk import Labeller
     lab = Labeller(0)
+    lab.set_small_path(request.param[1])
+    yield lab
+    lab.close()
+
+
+@pytest.fixture(scope="module")
+def cluster_labeller():
+    from paper_1405_1931_gb300.hk import Labeller
+    lab = Labeller(0)
+    lab.set_small_path(3)
     yield lab
     lab.close()
 
@@ -151,3 +165,88 @@ def test_small_capacity_rule(labeller):
     assert e.value.status == hk.HK_ERR_CAPACITY
     np.testing.assert_array_equal(short[0].cpu().numpy(), want[0])
     assert int(short[3].item()) == n
+
+
+CLUSTER_SHAPES = [(64, 64, 64), (96, 32, 48), (64, 1, 4096), (40, 70, 30), (1, 2048, 4), (33, 8, 500),
+                  (3, 5, 7), (32, 1, 9)]
+
+
+def cluster_fits(nx, ny, nz):
+    """The cluster kernel's limit as include/hk.h states it: the rows cut into 8 equal
+    blocks come to at most 1024 row segments (32 sites along x) a block."""
+    return -(-ny * nz // 8) * -(-nx // 32) <= 1024
+
+
+@pytest.mark.parametrize("shape", CLUSTER_SHAPES)
+def test_cluster_shapes(cluster_labeller, shape):
+    """Lattices the one-CTA kernel cannot hold (and a few tiny ones, with CTAs left
+    without rows): rows split unevenly over the 8 CTAs, rows crossing CTAs through every
+    periodic edge, the segment limit of a CTA reached exactly."""
+    nx, ny, nz = shape
+    assert cluster_fits(nx, ny, nz)
+    for i, p in enumerate((0.2, 0.3116, 0.55)):
+        phi = fields.iid_field(nx, ny, nz, seed=61 + i, occupancy=p)
+        for per in [(1, 1, 1), (0, 0, 0), (1, 0, 1), (0, 1, 1)]:
+            assert_parity(cluster_labeller, phi, per, f"{shape} p={p} per={per}")
+
+
+def test_cluster_special_patterns(cluster_labeller):
+    # the site checkerboard at 64^3: 131072 clusters of one site, 16384 runs per CTA (the limit)
+    nx = ny = nz = 64
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    chk = np.where((x + y + z) % 2 == 0, 1.0, -1.0).astype(np.float32)
+    for per in [(1, 1, 1), (0, 0, 0)]:
+        assert_parity(cluster_labeller, chk, per, f"checkerboard 64^3 {per}")
+    # one cluster through every CTA: a serpentine along x and y in every plane, planes
+    # joined at one corner each, so the union chains cross every CTA boundary
+    phi = np.full((nz, ny, nx), -1.0, np.float32)
+    phi[:, ::2, :] = 1.0
+    phi[:, 1::4, -1] = 1.0
+    phi[:, 3::4, 0] = 1.0
+    assert_parity(cluster_labeller, phi, (0, 0, 0), "serpentine planes")
+    phi[:, :, :] = -1.0
+    phi[:, 0, 0] = 1.0        # a column along z: one cluster spanning all 8 CTAs, joined by the wrap
+    assert_parity(cluster_labeller, phi, (0, 0, 1), "z column periodic")
+    assert_parity(cluster_labeller, phi, (0, 0, 0), "z column open")
+    full = np.full((nz, ny, nx), 1.0, np.float32)
+    assert_parity(cluster_labeller, full, (1, 1, 1), "full")
+
+
+def test_cluster_limit_and_beyond():
+    """The largest lattice of each axis the cluster takes, and the first it does not
+    (that one takes the tiled passes); both against the oracle."""
+    from paper_1405_1931_gb300.hk import Labeller
+    lab = Labeller(0)
+    for shape, fits in [((32, 1, 8192), True), ((32, 1, 8193), False), ((65, 64, 64), False), ((64, 64, 65), False)]:
+        assert cluster_fits(*shape) == fits
+        phi = fields.iid_field(*shape, seed=71, occupancy=0.3116)
+        assert_parity(lab, phi, (1, 1, 1), f"cluster limit {shape}")
+    lab.close()
+
+
+def test_cluster_batches():
+    """Batches through the cluster kernel: a few lattices of mixed shapes (clusters by
+    default), and more lattices than the cluster threshold that only the cluster holds."""
+    from paper_1405_1931_gb300.hk import Labeller
+    lab = Labeller(0)
+    rng = np.random.default_rng(13)
+    for count, lo, hi in ((5, 8, 64), (20, 40, 64)):
+        items, phis, pers = [], [], []
+        for i in range(count):
+            shape = tuple(int(v) for v in rng.integers(lo, hi + 1, size=3))
+            phi = fields.iid_field(*shape, seed=800 + 37 * count + i, occupancy=float(rng.uniform(0.2, 0.5)))
+            per = tuple(int(v) for v in rng.integers(0, 2, size=3))
+            d = torch.from_numpy(phi).cuda()
+            items.append((d, per, lab.alloc_outputs(d.shape, d.device)))
+            phis.append(phi)
+            pers.append(per)
+        lab.label_batched(items)
+        lab.sync_status()
+        for (d, per, (labels, sizes, hist, ncl, cap)), phi in zip(items, phis):
+            want = oracle.label(phi, per)
+            n = int(ncl.item())
+            assert n == want[3]
+            np.testing.assert_array_equal(labels.cpu().numpy(), want[0])
+            np.testing.assert_array_equal(sizes[:n].cpu().numpy(), want[1])
+            np.testing.assert_array_equal(hist.cpu().numpy(), want[2])
+    lab.close()
