@@ -18,6 +18,7 @@
 // clusters by label.  No workspace is used: the results go straight to the outputs.
 #include <cooperative_groups.h>
 
+#include <cstddef>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -247,11 +248,15 @@ struct ClusterSmem {
     int sz[CRUN];            // piece size, summed at each root; after ranking: the root's site
     uint16_t desc[CRUN];     // per run: (local segment << 5) | first x, and DESC_LROOT
     int roots;               // cluster roots among this CTA's runs
+    uint64_t bar;            // completion of the bulk copy of this CTA's rows of phi
     int warp_tmp[32];
     int scan_total;
     int hist[32];
 };
 static_assert(sizeof(ClusterSmem) <= 227 * 1024, "one CTA's shared memory");
+static_assert(offsetof(ClusterSmem, sz) == offsetof(ClusterSmem, par) + sizeof(int) * CRUN &&
+                  sizeof(int) * 2 * CRUN >= sizeof(float) * TX * CSEG,
+              "par and sz together hold a CTA's rows of phi");
 
 namespace cg = cooperative_groups;
 
@@ -325,9 +330,43 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(CNT, 1)
     const int cbase = c << CRUN_BITS;
     if (tid < 32) S.hist[tid] = 0;
 
-    // a1: occupancy words of this CTA's segments, 32 loads in flight per warp
+    // a1: occupancy words of this CTA's segments.  Its rows of phi are one contiguous
+    // range: one bulk copy lands it in par and sz (not in use yet) when it is 16-byte
+    // aligned, and each warp turns landed segments into words by ballots; otherwise (or
+    // if the copy does not complete within its bound) 32 loads in flight per warp.
+    bool landed = false;
+    {
+        const float *src = L.phi + (int64_t)q0 * nx;
+        const int nfl = (q1 - q0) * nx;
+        if (nfl > 0 && (nfl & 3) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {   // uniform
+            const float *land = reinterpret_cast<const float *>(S.par);
+            if (tid == 0) {
+                mbar_init(&S.bar, 1);
+                fence_mbar_init();
+            }
+            __syncthreads();
+            if (tid == 0) {
+                mbar_arrive_expect_tx(&S.bar, (uint32_t)nfl * 4u);
+                bulk_load(S.par, src, (uint32_t)nfl * 4u, &S.bar);
+            }
+            landed = mbar_wait_bounded(&S.bar, 0);
+            if (__syncthreads_or(!landed)) {
+                if (tid == 0) atomicOr(status, STATUS_TMA_TIMEOUT);
+                mbar_wait_bounded(&S.bar, 0);   // the copy still in flight
+                landed = false;
+            } else {
+                landed = true;
+                for (int ls = wid; ls < nseg; ls += NW) {
+                    const int r = (int)div_nbx((uint32_t)ls), x = (ls - r * nbx) * 32 + lane;
+                    const float v = x < nx ? land[r * nx + x] : 0.0f;
+                    const uint32_t w = __ballot_sync(0xffffffffu, occupied(v, L.occ_mode));
+                    if (lane == 0) S.m[ls] = w;
+                }
+            }
+        }
+    }
     constexpr int INF = 32;
-    for (int l0 = wid; l0 < nseg; l0 += NW * INF) {
+    for (int l0 = landed ? nseg : wid; l0 < nseg; l0 += NW * INF) {
         float v[INF];
 #pragma unroll
         for (int j = 0; j < INF; ++j) {
@@ -467,20 +506,25 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(CNT, 1)
         if (S.desc[i] & DESC_LROOT) S.par[i] = V.find_ro(cbase | i);
     __syncthreads();
 
-    // compression and piece sizes: a run's cluster root is its local root's (two reads
-    // of this CTA's shared memory); the run lengths of a group of lanes with the same
-    // root are added once, at the root's CTA
+    // piece sizes: every run's length goes to its local root, in this CTA's shared
+    // memory; a local root that is not its cluster's root then passes its sum on to the
+    // cluster root, once per group of lanes with the same cluster root
+    for (int i = tid; i < total; i += CNT) {
+        const int d = S.desc[i];
+        const int lr = (d & DESC_LROOT) ? i : (S.par[i] & (CRUN - 1));
+        atomicAdd(&S.sz[lr], run_len(S.m[(d & ~DESC_LROOT) >> 5], d & 31));
+    }
+    __syncthreads();
     for (int i0 = 0; i0 < total; i0 += CNT) {   // warp-uniform trips
         const int i = i0 + tid;
-        int root = -1, len = 0;
-        if (i < total) {
-            const int d = S.desc[i];
-            root = (d & DESC_LROOT) ? S.par[i] : S.par[S.par[i] & (CRUN - 1)];
-            len = run_len(S.m[(d & ~DESC_LROOT) >> 5], d & 31);
+        int root = -1, sum = 0;
+        if (i < total && (S.desc[i] & DESC_LROOT) && S.par[i] != (cbase | i)) {
+            root = S.par[i];
+            sum = S.sz[i];
         }
         const unsigned peers = __match_any_sync(0xffffffffu, root);
-        const int sum = (int)__reduce_add_sync(peers, (unsigned)len);
-        if (root >= 0 && lane == __ffs(peers) - 1) atomicAdd(V.sz(root), sum);
+        const int tot = (int)__reduce_add_sync(peers, (unsigned)sum);
+        if (root >= 0 && lane == __ffs(peers) - 1) atomicAdd(V.sz(root), tot);
     }
     __syncthreads();
     for (int i = tid; i < total; i += CNT)   // every run now points at its cluster root
