@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(SNT, 1) k_small_label(const __grid_constant__ 
 // CTAs are separated by cluster barriers.
 // ---------------------------------------------------------------------------------------
 constexpr int CS = 8;              // CTAs per lattice (a portable cluster size)
-constexpr int CNT = 512;           // threads per CTA
+constexpr int CNT = 1024;          // threads per CTA
 constexpr int CSEG = 1024;         // row segments per CTA
 constexpr int CRUN_BITS = 14;
 constexpr int CRUN = 1 << CRUN_BITS;   // runs per CTA: at most 16 per segment
