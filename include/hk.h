@@ -391,9 +391,11 @@ int hk_set_merge(hk_ctx *ctx, int unions_per_lane, int combine_hot);
  * kernel, in shared memory, with no workspace.  Two kernels:
  *   - one CTA holds a lattice of at most 32768 sites and 2048 row segments of 32
  *     sites along x (nx rounded up to a multiple of 32, times ny * nz);
- *   - a thread-block cluster of 8 CTAs on 8 SMs holds a lattice whose ny * nz rows,
- *     cut into 8 equal blocks, come to at most 1024 row segments a block (64^3
- *     fits); the CTAs reach each other's runs through distributed shared memory.
+ *   - a thread-block cluster of CS CTAs on CS SMs holds a lattice whose ny * nz
+ *     rows, cut into CS equal blocks, come to at most 1024 row segments a block;
+ *     CS is 16 where the device co-schedules clusters that large, else 8 (64^3
+ *     fits either way); the CTAs reach each other's runs through distributed
+ *     shared memory.
  * hk_label, hk_label_host(_async) and hk_label_batched take this path when every
  * lattice of the call fits: the cluster kernel for calls of at most 16 lattices that
  * all fit it, else one CTA per lattice where they all fit that; 64 lattices per

@@ -85,13 +85,15 @@ constexpr int SMALL_MAX_SITES = 32768;
 constexpr int SMALL_MAX_SEG = 2048;
 constexpr int SMALL_MAX_RUNS = 16384 + 2048;
 bool small_fits(int nx, int ny, int nz);
-// The cluster form (hk_small.cu): CS = 8 CTAs on 8 SMs label one lattice whose rows,
-// split into 8 equal blocks, come to at most 1024 row segments a block (64^3 fits).
+// The cluster form (hk_small.cu): a cluster of CS CTAs on CS SMs labels one lattice
+// whose rows, split into CS equal blocks, come to at most 1024 row segments a block.
+// CS is 16 where the device co-schedules a cluster that large, else 8 (64^3 fits
+// either way); cluster_fits applies this device's CS.
 bool cluster_fits(int nx, int ny, int nz);
 // whether this device can run the cluster form (checked once per device)
 bool cluster_ok();
 // n lattices that all fit the chosen form (n <= MAX_LAT_PER_LAUNCH): one CTA each, or with
-// cluster (after cluster_ok()) one cluster of 8 CTAs each; every lat[i].ncl must be a
+// cluster (after cluster_ok()) one cluster of CS CTAs each; every lat[i].ncl must be a
 // device int64.  status: the device status word; local_cap as in Work.
 cudaError_t launch_small(const LatDev *lats, int n, int32_t *status, int32_t local_cap, cudaStream_t st,
                          bool cluster);

@@ -233,7 +233,8 @@ __global__ void __launch_bounds__(SNT, 1) k_small_label(const __grid_constant__ 
 // each run's label is resolved once per run, not per site.  The phases that reach other
 // CTAs are separated by cluster barriers.
 // ---------------------------------------------------------------------------------------
-constexpr int CS = 8;              // CTAs per lattice (a portable cluster size)
+// CTAs per lattice: 16 where the device co-schedules that many (a non-portable cluster
+// size), else 8 (the portable size); a template parameter of the kernel (CSB = log2).
 constexpr int CNT = 1024;          // threads per CTA
 constexpr int CSEG = 1024;         // row segments per CTA
 constexpr int CRUN_BITS = 14;
@@ -311,9 +312,10 @@ struct ClusterView {
     }
 };
 
-template <int NL>
-__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(CNT, 1)
+template <int CSB, int NL>
+__global__ void __cluster_dims__(1 << CSB, 1, 1) __launch_bounds__(CNT, 1)
     k_small_cluster(const __grid_constant__ LatBatch<NL> B, int32_t *status, int32_t local_cap) {
+    constexpr int CS_BITS = CSB, CS = 1 << CSB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ClusterSmem &S = *reinterpret_cast<ClusterSmem *>(smem_raw);
     cg::cluster_group cl = cg::this_cluster();
@@ -464,19 +466,20 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(CNT, 1)
             for (int h = 0; h < 2; ++h)
                 if (2 * tid + h < nseg)
                     pairs(2 * tid + h, cross, [&](int a, int o, int bb) {
-                        S.sz[j++] = (a << (CRUN_BITS + 3)) | (o << CRUN_BITS) | bb;
+                        S.sz[j++] = (int)(((uint32_t)a << (CRUN_BITS + CS_BITS)) | ((uint32_t)o << CRUN_BITS) | (uint32_t)bb);
                     });
             __syncthreads();
             for (int k = tid; k < npairs; k += CNT) {
                 const int v = S.sz[k];
-                join(v >> (CRUN_BITS + 3), (v >> CRUN_BITS) & 7, v & (CRUN - 1));
+                const uint32_t u = (uint32_t)v;
+                join((int)(u >> (CRUN_BITS + CS_BITS)), (int)((u >> CRUN_BITS) & (CS - 1)), (int)(u & (CRUN - 1)));
             }
         } else {
             for (int h = 0; h < 2; ++h)
                 if (2 * tid + h < nseg) pairs(2 * tid + h, cross, join);
         }
     };
-    static_assert(CS <= 8 && 2 * CRUN_BITS + 3 <= 31, "a listed pair packs into one int");
+    static_assert(2 * CRUN_BITS + CS_BITS <= 32 && CS <= 32, "a listed pair packs into 32 bits");
     {
         const int lcap = (local_cap > 0 && local_cap < total) ? local_cap : total;
         round(false, [&](int a, int, int bb) { s_union(S.par, a, bb, lcap, status); });
@@ -611,44 +614,80 @@ bool small_fits(int nx, int ny, int nz) {
     return N <= SMALL_MAX_SITES && nseg <= SMALL_MAX_SEG;
 }
 
-bool cluster_fits(int nx, int ny, int nz) {
-    const int64_t nbx = (nx + TX - 1) / TX, rows = (int64_t)ny * nz;
-    return nx >= 1 && ny >= 1 && nz >= 1 && ((rows + CS - 1) / CS) * nbx <= CSEG;
-}
-
-bool cluster_ok() {
+// log2 of the cluster size this device runs the cluster kernel with (4 or 3), or 0 if
+// it cannot run it; checked once per device
+static int cluster_bits() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
         cudaGetLastError();
-        return false;
+        return 0;
     }
-    static int state[MAX_DEVICES];   // 0 unknown, 1 the cluster kernel can run, 2 it cannot
+    static int state[MAX_DEVICES];   // -1 unknown, else the cluster bits (0: none)
+    static bool init = false;
     static std::mutex mu;
     std::lock_guard<std::mutex> lock(mu);
-    if (!state[dev]) {
-        bool ok = cudaFuncSetAttribute(k_small_cluster<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(ClusterSmem)) == cudaSuccess &&
-                  cudaFuncSetAttribute(k_small_cluster<MAX_LAT_PER_LAUNCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(ClusterSmem)) == cudaSuccess;
-        if (ok) {   // at least one cluster of CS CTAs with this much shared memory fits the device
+    if (!init) {
+        for (int &v : state) v = -1;
+        init = true;
+    }
+    if (state[dev] < 0) {
+        auto fits = [](auto k1, auto kn, int cs) {   // the kernels take the attributes, and a cluster fits
+            if (cs > 8 && (cudaFuncSetAttribute(k1, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+                           cudaFuncSetAttribute(kn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess))
+                return false;
+            if (cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ClusterSmem)) !=
+                    cudaSuccess ||
+                cudaFuncSetAttribute(kn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ClusterSmem)) !=
+                    cudaSuccess)
+                return false;
             cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3(CS, 1, 1);
+            cfg.gridDim = dim3(cs, 1, 1);
             cfg.blockDim = dim3(CNT, 1, 1);
             cfg.dynamicSmemBytes = sizeof(ClusterSmem);
             cudaLaunchAttribute attr;
             attr.id = cudaLaunchAttributeClusterDimension;
-            attr.val.clusterDim.x = CS;
+            attr.val.clusterDim.x = cs;
             attr.val.clusterDim.y = 1;
             attr.val.clusterDim.z = 1;
             cfg.attrs = &attr;
             cfg.numAttrs = 1;
             int nclusters = 0;
-            ok = cudaOccupancyMaxActiveClusters(&nclusters, k_small_cluster<1>, &cfg) == cudaSuccess && nclusters > 0;
-        }
-        if (!ok) cudaGetLastError();
-        state[dev] = ok ? 1 : 2;
+            return cudaOccupancyMaxActiveClusters(&nclusters, k1, &cfg) == cudaSuccess && nclusters > 0;
+        };
+        int bits = 0;
+        if (fits(k_small_cluster<4, 1>, k_small_cluster<4, MAX_LAT_PER_LAUNCH>, 16)) bits = 4;
+        else if (fits(k_small_cluster<3, 1>, k_small_cluster<3, MAX_LAT_PER_LAUNCH>, 8)) bits = 3;
+        cudaGetLastError();
+        state[dev] = bits;
     }
-    return state[dev] == 1;
+    return state[dev];
+}
+
+bool cluster_ok() { return cluster_bits() > 0; }
+
+bool cluster_fits(int nx, int ny, int nz) {
+    const int cs = 1 << cluster_bits();
+    const int64_t nbx = (nx + TX - 1) / TX, rows = (int64_t)ny * nz;
+    return cluster_bits() > 0 && nx >= 1 && ny >= 1 && nz >= 1 && ((rows + cs - 1) / cs) * nbx <= CSEG;
+}
+
+template <int CSB>
+static void launch_cluster(const LatDev *lats, int n, int32_t *status, int32_t local_cap, cudaStream_t st) {
+    constexpr int CS = 1 << CSB;
+    if (n == 1) {
+        LatBatch<1> B;
+        std::memset(&B, 0, sizeof(B));
+        B.n = 1;
+        B.lat[0] = lats[0];
+        k_small_cluster<CSB, 1><<<CS, CNT, sizeof(ClusterSmem), st>>>(B, status, local_cap);
+    } else {
+        LatBatch<MAX_LAT_PER_LAUNCH> B;
+        std::memset(&B, 0, sizeof(B));
+        B.n = n;
+        for (int i = 0; i < n; ++i) B.lat[i] = lats[i];
+        k_small_cluster<CSB, MAX_LAT_PER_LAUNCH><<<(unsigned)(CS * n), CNT, sizeof(ClusterSmem), st>>>(B, status,
+                                                                                                    local_cap);
+    }
 }
 
 cudaError_t launch_small(const LatDev *lats, int n, int32_t *status, int32_t local_cap, cudaStream_t st,
@@ -659,21 +698,11 @@ cudaError_t launch_small(const LatDev *lats, int n, int32_t *status, int32_t loc
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
-    if (cluster) {   // cluster_ok() has set the kernels' shared-memory attribute
-        if (n == 1) {
-            LatBatch<1> B;
-            std::memset(&B, 0, sizeof(B));
-            B.n = 1;
-            B.lat[0] = lats[0];
-            k_small_cluster<1><<<CS, CNT, sizeof(ClusterSmem), st>>>(B, status, local_cap);
-        } else {
-            LatBatch<MAX_LAT_PER_LAUNCH> B;
-            std::memset(&B, 0, sizeof(B));
-            B.n = n;
-            for (int i = 0; i < n; ++i) B.lat[i] = lats[i];
-            k_small_cluster<MAX_LAT_PER_LAUNCH><<<(unsigned)(CS * n), CNT, sizeof(ClusterSmem), st>>>(B, status,
-                                                                                                      local_cap);
-        }
+    if (cluster) {   // cluster_bits() has set the kernels' attributes
+        const int bits = cluster_bits();
+        if (bits == 4) launch_cluster<4>(lats, n, status, local_cap, st);
+        else if (bits == 3) launch_cluster<3>(lats, n, status, local_cap, st);
+        else return cudaErrorNotSupported;
         return cudaGetLastError();
     }
     static bool attr_set[MAX_DEVICES][2];

@@ -1,9 +1,10 @@
 """The one-launch path for small lattices against the oracle, element by element.
 
 Two kernels (hk_small.cu): one CTA holds a lattice of at most 32768 sites and 2048
-row segments in shared memory; a cluster of 8 CTAs holds a lattice whose rows, cut
-into 8 blocks, come to at most 1024 row segments a block, the CTAs reaching each
-other's runs through distributed shared memory.  Under each kernel alone, labels,
+row segments in shared memory; a cluster of 16 CTAs (8 where the device cannot
+co-schedule 16) holds a lattice whose rows, cut into that many blocks, come to at
+most 1024 row segments a block, the CTAs reaching each other's runs through
+distributed shared memory.  Under each kernel alone, labels,
 sizes, histogram and count must equal the oracle's exactly on every shape and
 periodic set it takes: axes of length 1 and 2, ragged x, the size limits, the site
 checkerboard with its V/2 clusters at the limit, empty and full lattices, and
@@ -168,13 +169,14 @@ def test_small_capacity_rule(labeller):
 
 
 CLUSTER_SHAPES = [(64, 64, 64), (96, 32, 48), (64, 1, 4096), (40, 70, 30), (1, 2048, 4), (33, 8, 500),
-                  (3, 5, 7), (32, 1, 9)]
+                  (3, 5, 7), (32, 1, 9), (64, 96, 80)]
 
 
-def cluster_fits(nx, ny, nz):
-    """The cluster kernel's limit as include/hk.h states it: the rows cut into 8 equal
-    blocks come to at most 1024 row segments (32 sites along x) a block."""
-    return -(-ny * nz // 8) * -(-nx // 32) <= 1024
+def cluster_fits(nx, ny, nz, blocks=8):
+    """The cluster kernel's limit as include/hk.h states it: the rows cut into equal
+    blocks (8, or 16 on a device that runs clusters of 16) come to at most 1024 row
+    segments (32 sites along x) a block."""
+    return -(-ny * nz // blocks) * -(-nx // 32) <= 1024
 
 
 @pytest.mark.parametrize("shape", CLUSTER_SHAPES)
@@ -183,7 +185,7 @@ def test_cluster_shapes(cluster_labeller, shape):
     without rows): rows split unevenly over the 8 CTAs, rows crossing CTAs through every
     periodic edge, the segment limit of a CTA reached exactly."""
     nx, ny, nz = shape
-    assert cluster_fits(nx, ny, nz)
+    assert cluster_fits(nx, ny, nz, blocks=16)
     for i, p in enumerate((0.2, 0.3116, 0.55)):
         phi = fields.iid_field(nx, ny, nz, seed=61 + i, occupancy=p)
         for per in [(1, 1, 1), (0, 0, 0), (1, 0, 1), (0, 1, 1)]:
@@ -213,12 +215,14 @@ def test_cluster_special_patterns(cluster_labeller):
 
 
 def test_cluster_limit_and_beyond():
-    """The largest lattice of each axis the cluster takes, and the first it does not
-    (that one takes the tiled passes); both against the oracle."""
+    """Lattices at the cluster kernel's limits -- the largest that fit 8 blocks, the
+    largest that fit 16 (a device that runs clusters of 8 labels these with the tiled
+    passes) -- and the first beyond both (the tiled passes); all against the oracle."""
     from paper_1405_1931_gb300.hk import Labeller
     lab = Labeller(0)
-    for shape, fits in [((32, 1, 8192), True), ((32, 1, 8193), False), ((65, 64, 64), False), ((64, 64, 65), False)]:
-        assert cluster_fits(*shape) == fits
+    for shape, fits8 in [((32, 1, 8192), True), ((32, 1, 8193), False), ((64, 64, 65), False), ((32, 1, 16384), False),
+                         ((32, 1, 16385), False), ((64, 128, 128), False)]:
+        assert cluster_fits(*shape) == fits8
         phi = fields.iid_field(*shape, seed=71, occupancy=0.3116)
         assert_parity(lab, phi, (1, 1, 1), f"cluster limit {shape}")
     lab.close()
