@@ -213,6 +213,13 @@ __device__ __forceinline__ int run_len(uint32_t m, int x0) {
 }
 
 // ---- PTX helpers ----------------------------------------------------------------------
+// Programmatic dependent launch: the kernels of the labelling sequence are launched so
+// that one may be set up while the previous one is still finishing.  Each waits here,
+// before its first access to global memory, until the previous kernel of the stream has
+// completed and its writes are visible (a kernel launched without that attribute
+// returns at once).
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }

@@ -33,6 +33,7 @@ namespace hk {
 // --------------------------------------------------------------------------------------
 template <int TY, int TZ, int NL>
 __global__ void __launch_bounds__(256, 4) k_occupancy(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
+    grid_dep_wait();
     using SH = TileShape<TY, TZ>;
     constexpr int R = SH::R, U = 16;
     const int lane = threadIdx.x & 31;
@@ -114,6 +115,7 @@ struct OccSmem {
 template <int TY, int TZ, int NL>
 __global__ void __launch_bounds__(256) k_occupancy_tma(const __grid_constant__ TmapBatch<NL> TB,
                                                        const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
+    grid_dep_wait();
     using SH = TileShape<TY, TZ>;
     constexpr int R = SH::R;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -219,6 +221,7 @@ struct LabelCfg {
 template <int TY, int TZ, int NL, bool FAST>
 __global__ void __launch_bounds__(TY * TZ, (LabelCfg<TY, TZ, FAST>::BLOCKS))
 k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
+    grid_dep_wait();
     using SH = TileShape<TY, TZ>;
     constexpr int R = SH::R, NT = SH::NT, MR = SH::MAXRUNS, CAP = LabelCfg<TY, TZ, FAST>::CAP;
     constexpr int BL = LabelCfg<TY, TZ, FAST>::BL;
@@ -562,6 +565,7 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
 template <int TY, int TZ, int NL, int U>
 __global__ void __launch_bounds__(256)
 k_face_merge(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
+    grid_dep_wait();
     using SH = TileShape<TY, TZ>;
     constexpr int C = 2 * U;   // U unions, 2 U find chains per lane and step
     const int lane = threadIdx.x & 31;
@@ -642,6 +646,7 @@ k_face_merge(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
 template <int NL, bool HOT>
 __global__ void __launch_bounds__(256)
 k_piece_finalize(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
+    grid_dep_wait();
     __shared__ int hot_target[8];   // per warp: the cluster root its pieces fed most, and the sum
     __shared__ int hot_sum[8];
     const int64_t t = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -731,6 +736,7 @@ __device__ __forceinline__ uint32_t row_roots(const LatBatch<NL> &B, const uint8
 template <int NL>
 __global__ void __launch_bounds__(SCAN_NT) k_scan_reduce(const __grid_constant__ LatBatch<NL> B,
                                                          const uint8_t *cnt, int64_t n, uint32_t *bsum) {
+    grid_dep_wait();
     __shared__ uint32_t red[SCAN_NT / 32];
     const int64_t b0 = (int64_t)blockIdx.x * SCAN_CH;
     uint32_t s = 0;
@@ -750,6 +756,7 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_reduce(const __grid_constant__
 
 // single block: exclusive scan of the block sums in place
 __global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t *bsum, int64_t nb) {
+    grid_dep_wait();
     __shared__ uint32_t wsum[32];
     __shared__ uint32_t carry;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -785,6 +792,7 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t *bsum, int64_t nb
 template <int NL>
 __global__ void __launch_bounds__(SCAN_NT) k_scan_apply(const __grid_constant__ LatBatch<NL> B, const uint8_t *cnt,
                                                         int64_t n, const uint32_t *bsum, uint32_t *pre) {
+    grid_dep_wait();
     __shared__ uint32_t wsum[SCAN_NT / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t b0 = (int64_t)blockIdx.x * SCAN_CH + (int64_t)threadIdx.x * SCAN_PER;
@@ -824,6 +832,7 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_apply(const __grid_constant__ 
 // per-lattice: cluster count from the prefix, clear the histogram
 template <int NL>
 __global__ void k_lattice_finish(const __grid_constant__ LatBatch<NL> B, Work W) {
+    grid_dep_wait();
     const int l = blockIdx.x;
     if (l >= B.n) return;
     const LatDev &L = B.lat[l];
@@ -869,6 +878,7 @@ __device__ __forceinline__ int site_of(const TileGeo &g, const LatDev &L, int po
 template <int TY, int TZ, int NL, bool SLAB>
 __global__ void __launch_bounds__(TY * TZ, 1280 / (TY * TZ))
 k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapBatch<NL> TB, Work W, int64_t ntiles) {
+    grid_dep_wait();
     using SH = TileShape<TY, TZ>;
     constexpr int R = SH::R, NT = SH::NT, NW = NT / 32, MR = SH::MAXRUNS;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1297,6 +1307,28 @@ cudaError_t launch_copy_counted(const int64_t *src, const int64_t *count, int64_
 // --------------------------------------------------------------------------------------
 // launch sequence
 // --------------------------------------------------------------------------------------
+// A kernel of the sequence, launched so that it may be set up while the previous kernel of
+// the stream finishes (programmatic dependent launch; the kernel's grid_dep_wait()
+// orders it after that kernel).  The first launch error of a sequence is kept in
+// launch_error for launch_all to return.
+static thread_local cudaError_t launch_error = cudaSuccess;
+template <typename... KArgs, typename... Args>
+static void launch_dep(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                       Args... args) {
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid, 1, 1);
+    cfg.blockDim = dim3(block, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, args...);
+    if (e != cudaSuccess && launch_error == cudaSuccess) launch_error = e;
+}
+
 template <typename K>
 static int persistent_grid(K kernel, int threads, size_t smem, int64_t ntiles) {
     int dev = 0, nsm = 0, per = 0;
@@ -1370,41 +1402,44 @@ static cudaError_t launch_all(const LatDev *lats, int n, const Plan &P, const Wo
     }
     const unsigned g4 = (unsigned)(P.ntiles < grid4 ? P.ntiles : grid4);
     auto mark = [&](int i) { if (ev) cudaEventRecord(ev[i], st); };
+    launch_error = cudaSuccess;
     mark(0);
     if (all_tma) {
         const unsigned g0 = (unsigned)(P.ntiles < grid0 ? P.ntiles : grid0);
-        k_occupancy_tma<TY, TZ, NL><<<g0, 256, smem0, st>>>(TB, B, W, P.ntiles);
+        launch_dep(k_occupancy_tma<TY, TZ, NL>, g0, 256, smem0, st, TB, B, W, P.ntiles);
     } else {
-        k_occupancy<TY, TZ, NL><<<(unsigned)((P.ntiles + 7) / 8), 256, 0, st>>>(B, W, P.ntiles);
+        launch_dep(k_occupancy<TY, TZ, NL>, (unsigned)((P.ntiles + 7) / 8), 256, 0, st, B, W, P.ntiles);
     }
     mark(1);
-    k_tile_label<TY, TZ, NL, true><<<(unsigned)P.ntiles, SH::NT, smem1, st>>>(B, W, P.ntiles);
+    launch_dep(k_tile_label<TY, TZ, NL, true>, (unsigned)P.ntiles, SH::NT, smem1, st, B, W, P.ntiles);
     // the tiles handed on (none for fields with at most MR_FAST / R runs a row on average)
-    k_tile_label<TY, TZ, NL, false><<<(unsigned)(P.ntiles < grid1b ? P.ntiles : grid1b), SH::NT, smem1b, st>>>(
-        B, W, P.ntiles);
+    launch_dep(k_tile_label<TY, TZ, NL, false>, (unsigned)(P.ntiles < grid1b ? P.ntiles : grid1b), SH::NT, smem1b, st,
+               B, W, P.ntiles);
     mark(2);
     const unsigned gm = (unsigned)((P.ntiles + 7) / 8);
-    if (ms.unions == 1) k_face_merge<TY, TZ, NL, 1><<<gm, 256, 0, st>>>(B, W, P.ntiles);
-    else if (ms.unions == 4) k_face_merge<TY, TZ, NL, 4><<<gm, 256, 0, st>>>(B, W, P.ntiles);
-    else k_face_merge<TY, TZ, NL, 2><<<gm, 256, 0, st>>>(B, W, P.ntiles);
+    if (ms.unions == 1) launch_dep(k_face_merge<TY, TZ, NL, 1>, gm, 256, 0, st, B, W, P.ntiles);
+    else if (ms.unions == 4) launch_dep(k_face_merge<TY, TZ, NL, 4>, gm, 256, 0, st, B, W, P.ntiles);
+    else launch_dep(k_face_merge<TY, TZ, NL, 2>, gm, 256, 0, st, B, W, P.ntiles);
     mark(3);
-    if (ms.hot) k_piece_finalize<NL, true><<<gm, 256, 0, st>>>(B, W, P.ntiles);
-    else k_piece_finalize<NL, false><<<gm, 256, 0, st>>>(B, W, P.ntiles);
+    if (ms.hot) launch_dep(k_piece_finalize<NL, true>, gm, 256, 0, st, B, W, P.ntiles);
+    else launch_dep(k_piece_finalize<NL, false>, gm, 256, 0, st, B, W, P.ntiles);
     mark(4);
     const int64_t nb = (P.nrows + SCAN_CH) / SCAN_CH;   // covers index nrows (the total)
-    k_scan_reduce<NL><<<(unsigned)nb, SCAN_NT, 0, st>>>(B, W.cnt, P.nrows, W.bsum);
-    k_scan_blocks<<<1, 1024, 0, st>>>(W.bsum, nb);
-    k_scan_apply<NL><<<(unsigned)nb, SCAN_NT, 0, st>>>(B, W.cnt, P.nrows, W.bsum, W.pre);
+    launch_dep(k_scan_reduce<NL>, (unsigned)nb, SCAN_NT, 0, st, B, (const uint8_t *)W.cnt, P.nrows, W.bsum);
+    launch_dep(k_scan_blocks, 1u, 1024u, 0, st, W.bsum, nb);
+    launch_dep(k_scan_apply<NL>, (unsigned)nb, SCAN_NT, 0, st, B, (const uint8_t *)W.cnt, P.nrows,
+               (const uint32_t *)W.bsum, W.pre);
     mark(5);
-    k_lattice_finish<NL><<<(unsigned)n, 32, 0, st>>>(B, W);
+    launch_dep(k_lattice_finish<NL>, (unsigned)n, 32u, 0, st, B, W);
     mark(6);
     if constexpr (NL == 1) {
-        if (W.roots || W.site_off) k_flatten<TY, TZ, NL, true><<<g4, SH::NT, smem4, st>>>(B, TB, W, P.ntiles);
-        else k_flatten<TY, TZ, NL, false><<<g4, SH::NT, smem4, st>>>(B, TB, W, P.ntiles);
+        if (W.roots || W.site_off) launch_dep(k_flatten<TY, TZ, NL, true>, g4, SH::NT, smem4, st, B, TB, W, P.ntiles);
+        else launch_dep(k_flatten<TY, TZ, NL, false>, g4, SH::NT, smem4, st, B, TB, W, P.ntiles);
     } else {
-        k_flatten<TY, TZ, NL, false><<<g4, SH::NT, smem4, st>>>(B, TB, W, P.ntiles);
+        launch_dep(k_flatten<TY, TZ, NL, false>, g4, SH::NT, smem4, st, B, TB, W, P.ntiles);
     }
     mark(7);
+    if (launch_error != cudaSuccess) return launch_error;
     return cudaGetLastError();
 }
 
