@@ -297,15 +297,28 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
             if ((S.nxlo[r >> 5] >> (r & 31)) & 1u) conn |= 1u;
             if ((S.nxhi[r >> 5] >> (r & 31)) & 1u) conn |= 1u << g.lastX;
             conn &= m;
+            // The run starts whose run holds a connected site, for the whole row at once:
+            // conn is spread towards lower x inside each run by doubling (after the step
+            // of shift s, bit i holds the OR of conn over [i, i + 2s - 1] when m is set
+            // all the way from i; rr marks where m is set over [i, i + s]).
+            uint32_t f = conn, rr = m & (m >> 1);
+            f |= (f >> 1) & rr;
+            rr &= rr >> 1;
+            f |= (f >> 2) & rr;
+            rr &= rr >> 2;
+            f |= (f >> 4) & rr;
+            rr &= rr >> 4;
+            f |= (f >> 8) & rr;
+            rr &= rr >> 8;
+            f |= (f >> 16) & rr;
+            const uint32_t touched = f & rs;
             uint32_t w = rs;
             int id = rb;
             while (w) {
                 const int x0 = __ffs(w) - 1;
                 w &= w - 1;
-                const int len = run_len(m, x0);
-                const bool touch = ((conn >> x0) << (32 - len)) != 0;   // a connected site in the run
                 S.par[id] = id;
-                S.desc[id] = (uint16_t)((touch ? DESC_TOUCH : 0) | (r << 5) | x0);
+                S.desc[id] = (uint16_t)((((touched >> x0) & 1u) ? DESC_TOUCH : 0) | (r << 5) | x0);
                 ++id;
             }
         }
