@@ -239,8 +239,8 @@ def flush_l2(buf):
 
 
 def time_single(lab, phi, per, reps, flush=None):
-    """Device time (ms, median) of one hk_label call on a resident lattice, L2 flushed
-    between reps when `flush` is given, and the median latency of a call enqueued only
+    """Device time (ms, trimmed mean) of one hk_label call on a resident lattice, L2
+    flushed between reps when `flush` is given, and the latency of a call enqueued only
     once the device is idle (the host's enqueue then counts too).
 
     For the device time the reps are enqueued back to back (flush, event, call, event),
@@ -274,7 +274,16 @@ def time_single(lab, phi, per, reps, flush=None):
         b.synchronize()
         one.append(a.elapsed_time(b))
     lab.sync_status()
-    return float(np.median(dev)), int(out[3].item()), float(np.median(one))
+    return trimmed_mean(dev), int(out[3].item()), trimmed_mean(one)
+
+
+def trimmed_mean(ts, cut=0.1):
+    """Mean of the samples without the lowest and highest tenth.  CUDA event times come in
+    steps of about 2 us on this device, so a median of short calls can only move by a
+    step; a trimmed mean resolves finer changes and still drops outliers."""
+    v = np.sort(np.asarray(ts, dtype=np.float64))
+    k = int(len(v) * cut)
+    return float(v[k:len(v) - k].mean()) if len(v) > 2 * k else float(v.mean())
 
 
 def extra_configs(args, peak):
@@ -348,7 +357,7 @@ def extra_configs(args, peak):
             if mode == "idle_device":
                 b.synchronize()
         torch.cuda.synchronize()
-        times[mode] = float(np.median([a.elapsed_time(b) for a, b in ts]))
+        times[mode] = trimmed_mean([a.elapsed_time(b) for a, b in ts])
     ms = times["back_to_back"]
     ncl = int(res_i[3].item())
     tags = res_i[4][:ncl].cpu().numpy()

@@ -532,10 +532,11 @@ __global__ void __cluster_dims__(1 << CSB, 1, 1) __launch_bounds__(CNT, 1)
     __syncthreads();
     for (int i = tid; i < total; i += CNT)   // every run now points at its cluster root
         if (!(S.desc[i] & DESC_LROOT)) S.par[i] = S.par[S.par[i] & (CRUN - 1)];
-    cl.sync();
 
     // a4, a6, a7: the roots in run order get consecutive ranks; the roots of the CTAs
-    // before this one come first
+    // before this one come first.  The cluster roots (local roots pointing at
+    // themselves) are counted before the barrier that completes the sizes, which then
+    // publishes the counts too.
     const int per = (total + CNT - 1) / CNT;
     const int i0 = tid * per, i1 = min(i0 + per, total);
     int nr = 0;
