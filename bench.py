@@ -386,7 +386,7 @@ def extra_configs(args, peak):
     index2 = torch.from_numpy(I2).cuda()
     del I2, near
 
-    def ev_median(fn, reps=10):
+    def ev_time(fn, reps=10):   # calls enqueued back to back, as in time_single
         ts = []
         for _ in range(reps):
             flush_l2(flush)
@@ -394,18 +394,18 @@ def extra_configs(args, peak):
             a.record(s0)
             fn()
             b.record(s0)
-            b.synchronize()
-            ts.append(a.elapsed_time(b))
-        return float(np.median(ts))
+            ts.append((a, b))
+        torch.cuda.synchronize()
+        return trimmed_mean([a.elapsed_time(b) for a, b in ts])
 
     out_state = torch.empty_like(state)
     for _ in range(2):
         lab.interior_state(index, out=out_state)
-    ms_full = ev_median(lambda: lab.interior_state(index, out=out_state))
+    ms_full = ev_time(lambda: lab.interior_state(index, out=out_state))
     upd = torch.empty_like(state)
-    ms_dense = ev_median(lambda: hk.interior_update(state, index2, out=upd))
+    ms_dense = ev_time(lambda: hk.interior_update(state, index2, out=upd))
     sp = state.clone()
-    ms_sites = ev_median(lambda: hk.interior_update_sites(sp, sites, vals))
+    ms_sites = ev_time(lambda: hk.interior_update_sites(sp, sites, vals))
     full2 = lab.interior_state(index2)
     assert torch.equal(upd, full2) and torch.equal(sp, full2)     # the update equals a refresh
     n_int = int((full2 == 1).sum().item())
