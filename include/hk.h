@@ -397,9 +397,10 @@ int hk_set_merge(hk_ctx *ctx, int unions_per_lane, int combine_hot);
  *     fits either way); the CTAs reach each other's runs through distributed
  *     shared memory.
  * hk_label, hk_label_host(_async) and hk_label_batched take this path when every
- * lattice of the call fits: the cluster kernel for calls of at most 16 lattices that
- * all fit it, else one CTA per lattice where they all fit that; 64 lattices per
- * launch.  Results are identical to the tiled passes.  With timing on, such a call
+ * lattice of the call fits: the cluster kernel when they all fit it and their clusters
+ * take about half of the clusters the device holds at once, or fewer
+ * (cudaOccupancyMaxActiveClusters), else one CTA per lattice where they all fit that,
+ * else the cluster kernel; 64 lattices per launch.  Results are identical to the tiled passes.  With timing on, such a call
  * reports all its time as the first pass.  enable: 1 (default) as described; 0 this
  * context uses the tiled passes for every lattice; 2 the one-CTA kernel only; 3 the
  * cluster kernel only (for tests and comparisons; lattices the chosen kernel cannot

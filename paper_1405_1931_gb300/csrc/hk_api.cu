@@ -88,9 +88,6 @@ struct hk_ctx {
 namespace {
 
 constexpr int DEFAULT_TY = 16, DEFAULT_TZ = 16;
-// calls of at most this many small lattices take the cluster kernel (8 SMs each; more
-// lattices than the device holds clusters at once go one CTA each)
-constexpr int CLUSTER_MAX_LATTICES = 16;
 constexpr int64_t MAX_SITES = (int64_t)1 << 31;
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -308,8 +305,8 @@ int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st, bo
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return fail_cuda(ctx, e);
 
-    // Small lattices take one launch: a thread-block cluster of 8 CTAs per lattice for
-    // calls of a few lattices (latency: the work of a lattice spread over 8 SMs), one
+    // Small lattices take one launch: a thread-block cluster per lattice for calls of a
+    // few lattices (latency: the work of a lattice spread over the cluster's SMs), one
     // CTA per lattice for larger batches of lattices that fit it (throughput); up to
     // MAX_LAT_PER_LAUNCH lattices per launch.
     if (!index_field && ctx->small_path && !roots && site_off == 0) {
@@ -319,7 +316,10 @@ int run_lattices(hk_ctx *ctx, const hk_lattice *lats, int n, cudaStream_t st, bo
             all_cluster = all_cluster && hk::cluster_fits(lats[i].nx, lats[i].ny, lats[i].nz);
         }
         if (all_one || all_cluster) {
-            const bool cluster = all_cluster && (!all_one || n <= CLUSTER_MAX_LATTICES);
+            // clusters win while they fill about half of the device's cluster slots; past
+            // that, lattices that fit one CTA each finish sooner that way (measured at 32^3
+            // with 7 slots of 16 CTAs: 4 lattices 31 against 38 us, 8 lattices 48 against 39 us)
+            const bool cluster = all_cluster && (!all_one || 2 * n <= hk::cluster_slots() + 1);
             int rc_cap = HK_OK;
             for (int c0 = 0; c0 < n; c0 += hk::MAX_LAT_PER_LAUNCH) {
                 const int rc = run_small(ctx, lats + c0, std::min(n - c0, hk::MAX_LAT_PER_LAUNCH), st, check_capacity,

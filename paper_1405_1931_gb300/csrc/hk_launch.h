@@ -90,8 +90,10 @@ bool small_fits(int nx, int ny, int nz);
 // CS is 16 where the device co-schedules a cluster that large, else 8 (64^3 fits
 // either way); cluster_fits applies this device's CS.
 bool cluster_fits(int nx, int ny, int nz);
-// whether this device can run the cluster form (checked once per device)
+// whether this device can run the cluster form, and how many of its clusters the device
+// holds at once (checked once per device)
 bool cluster_ok();
+int cluster_slots();
 // n lattices that all fit the chosen form (n <= MAX_LAT_PER_LAUNCH): one CTA each, or with
 // cluster (after cluster_ok()) one cluster of CS CTAs each; every lat[i].ncl must be a
 // device int64.  status: the device status word; local_cap as in Work.

@@ -616,14 +616,15 @@ bool small_fits(int nx, int ny, int nz) {
 }
 
 // log2 of the cluster size this device runs the cluster kernel with (4 or 3), or 0 if
-// it cannot run it; checked once per device
-static int cluster_bits() {
+// it cannot run it, and how many such clusters it holds at once; checked once per device
+static int cluster_bits(int *slots_out = nullptr) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
         cudaGetLastError();
         return 0;
     }
     static int state[MAX_DEVICES];   // -1 unknown, else the cluster bits (0: none)
+    static int slots[MAX_DEVICES];   // clusters resident at once
     static bool init = false;
     static std::mutex mu;
     std::lock_guard<std::mutex> lock(mu);
@@ -632,7 +633,7 @@ static int cluster_bits() {
         init = true;
     }
     if (state[dev] < 0) {
-        auto fits = [](auto k1, auto kn, int cs) {   // the kernels take the attributes, and a cluster fits
+        auto fits = [](auto k1, auto kn, int cs, int &nclusters) {   // the kernels take the attributes, and a cluster fits
             if (cs > 8 && (cudaFuncSetAttribute(k1, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
                            cudaFuncSetAttribute(kn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess))
                 return false;
@@ -652,16 +653,24 @@ static int cluster_bits() {
             attr.val.clusterDim.z = 1;
             cfg.attrs = &attr;
             cfg.numAttrs = 1;
-            int nclusters = 0;
+            nclusters = 0;
             return cudaOccupancyMaxActiveClusters(&nclusters, k1, &cfg) == cudaSuccess && nclusters > 0;
         };
-        int bits = 0;
-        if (fits(k_small_cluster<4, 1>, k_small_cluster<4, MAX_LAT_PER_LAUNCH>, 16)) bits = 4;
-        else if (fits(k_small_cluster<3, 1>, k_small_cluster<3, MAX_LAT_PER_LAUNCH>, 8)) bits = 3;
+        int bits = 0, n = 0;
+        if (fits(k_small_cluster<4, 1>, k_small_cluster<4, MAX_LAT_PER_LAUNCH>, 16, n)) bits = 4;
+        else if (fits(k_small_cluster<3, 1>, k_small_cluster<3, MAX_LAT_PER_LAUNCH>, 8, n)) bits = 3;
         cudaGetLastError();
         state[dev] = bits;
+        slots[dev] = bits ? n : 0;
     }
+    if (slots_out) *slots_out = slots[dev];
     return state[dev];
+}
+
+int cluster_slots() {
+    int n = 0;
+    cluster_bits(&n);
+    return n;
 }
 
 bool cluster_ok() { return cluster_bits() > 0; }
