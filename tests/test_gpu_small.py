@@ -254,3 +254,42 @@ def test_cluster_batches():
             np.testing.assert_array_equal(sizes[:n].cpu().numpy(), want[1])
             np.testing.assert_array_equal(hist.cpu().numpy(), want[2])
     lab.close()
+
+
+@pytest.mark.parametrize("mode", [2, 3], ids=["one_cta", "cluster"])
+def test_small_kernels_capped_unions_report_or_are_exact(mode):
+    """With the union retries capped at one (hk_set_loop_cap), each call of a small-path
+    kernel either reports the cap through the status word or returns exact results; at
+    the natural bound every call is exact and the status stays clear."""
+    from paper_1405_1931_gb300 import hk
+    lab = hk.Labeller(0)
+    lab.set_small_path(mode)
+    shapes = [(32, 32, 32), (64, 64, 64)] if mode == 3 else [(32, 32, 32), (16, 32, 64)]
+    for shape in shapes:
+        for i, p in enumerate((0.3116, 0.45)):
+            phi = fields.iid_field(*shape, seed=90 + i, occupancy=p)
+            want = oracle.label(phi, (1, 1, 1))
+            lab.set_loop_cap(1)
+            got = gpu_label_raw(lab, phi, (1, 1, 1))
+            rc = hk.hk_sync_status(lab.ctx, hk._stream_handle(None))
+            assert rc in (hk.HK_OK, hk.HK_ERR_TIMEOUT)
+            if rc == hk.HK_OK:
+                assert got[3] == want[3]
+                np.testing.assert_array_equal(got[0], want[0])
+            lab.set_loop_cap(0)
+            got = gpu_label_raw(lab, phi, (1, 1, 1))
+            assert hk.hk_sync_status(lab.ctx, hk._stream_handle(None)) == hk.HK_OK
+            assert got[3] == want[3]
+            np.testing.assert_array_equal(got[0], want[0])
+            np.testing.assert_array_equal(got[1], want[1])
+            np.testing.assert_array_equal(got[2], want[2])
+    lab.close()
+
+
+def gpu_label_raw(lab, phi_np, per):
+    """Labels without reading the status word (the caller reads it)."""
+    phi = torch.from_numpy(np.ascontiguousarray(phi_np)).cuda()
+    labels, sizes, hist, ncl = lab.label(phi, per)
+    torch.cuda.synchronize()
+    n = int(ncl.item())
+    return labels.cpu().numpy(), sizes[:n].cpu().numpy(), hist.cpu().numpy(), n
