@@ -466,7 +466,8 @@ __global__ void __cluster_dims__(1 << CSB, 1, 1) __launch_bounds__(CNT, 1)
             for (int h = 0; h < 2; ++h)
                 if (2 * tid + h < nseg)
                     pairs(2 * tid + h, cross, [&](int a, int o, int bb) {
-                        S.sz[j++] = (int)(((uint32_t)a << (CRUN_BITS + CS_BITS)) | ((uint32_t)o << CRUN_BITS) | (uint32_t)bb);
+                        S.sz[j++] = (int)(((uint32_t)a << (CRUN_BITS + CS_BITS)) | ((uint32_t)o << CRUN_BITS) |
+                                          (uint32_t)bb);
                     });
             __syncthreads();
             for (int k = tid; k < npairs; k += CNT) {
@@ -633,7 +634,8 @@ static int cluster_bits(int *slots_out = nullptr) {
         init = true;
     }
     if (state[dev] < 0) {
-        auto fits = [](auto k1, auto kn, int cs, int &nclusters) {   // the kernels take the attributes, and a cluster fits
+        // the kernels take the attributes, and a cluster fits the device
+        auto fits = [](auto k1, auto kn, int cs, int &nclusters) {
             if (cs > 8 && (cudaFuncSetAttribute(k1, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
                            cudaFuncSetAttribute(kn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess))
                 return false;
@@ -720,7 +722,8 @@ cudaError_t launch_small(const LatDev *lats, int n, int32_t *status, int32_t loc
     std::lock_guard<std::mutex> lock(mu);
     if (n == 1) {
         if (!attr_set[dev][0]) {
-            e = cudaFuncSetAttribute(k_small_label<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SmallSmem));
+            e = cudaFuncSetAttribute(k_small_label<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sizeof(SmallSmem));
             if (e != cudaSuccess) return e;
             attr_set[dev][0] = true;
         }
