@@ -47,12 +47,13 @@ def test_batched_graph_replay_is_exact():
 
 def test_single_lattice_graph_replay_is_exact():
     """hk_label with graphs on: the first call runs and captures, later calls replay, on the
-    one-CTA path (32^3) and on the tiled passes (64 x 48 x 40)."""
+    one-launch path (32^3 and 64 x 48 x 40: a cluster kernel) and on the tiled passes
+    (160 x 96 x 64, dependent launches)."""
     from paper_1405_1931_gb300.hk import Labeller
     lab = Labeller(0)
     lab.set_graphs(True)
     s = torch.cuda.Stream()
-    for shape, per in [((32, 32, 32), (1, 1, 1)), ((64, 48, 40), (1, 0, 1))]:
+    for shape, per in [((32, 32, 32), (1, 1, 1)), ((64, 48, 40), (1, 0, 1)), ((160, 96, 64), (1, 1, 0))]:
         phi_np = fields.iid_field(*shape, seed=13, occupancy=0.3116)
         want = oracle.label(phi_np, per)
         phi = torch.from_numpy(phi_np).cuda()
