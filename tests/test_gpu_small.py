@@ -105,7 +105,10 @@ def test_small_special_patterns(labeller):
     assert_parity(labeller, phi, (1, 1, 1), "serpentine periodic")
 
 
-def test_just_beyond_the_limit_takes_the_tiled_passes(labeller):
+def test_just_beyond_the_one_cta_limit(labeller):
+    """Lattices just beyond the one-CTA kernel's limits: the one-CTA context labels them
+    with the tiled passes, the cluster context with the cluster kernel where they fit it
+    (the last, 32769 rows of one segment, fits neither)."""
     for shape in [(33, 993, 1), (32, 32, 33), (1, 1, 32769)]:
         phi = fields.iid_field(*shape, seed=7, occupancy=0.3116)
         for per in [(1, 1, 1), (0, 1, 0)]:
