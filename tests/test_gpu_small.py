@@ -132,7 +132,7 @@ def test_small_path_equals_tiled_passes():
 
 
 def test_small_batch_over_one_launch(labeller):
-    """100 small lattices (two launches of at most 64 CTAs), every output against the oracle."""
+    """100 small lattices (two launches of at most 64 lattices), every output against the oracle."""
     rng = np.random.default_rng(9)
     items, phis, pers = [], [], []
     for i in range(100):
