@@ -9,7 +9,7 @@ buffers resident on the device and:
 * admits requests while their bytes (field, labels, sizes and the per-lattice
   workspace bound) fit under a memory cap;
 * batches by size: arrived small requests go together into one batched call
-  (``hk_label_batched``) on a free high-priority worker stream, and requests
+  (``hk_label_batched``) on a free small-request worker stream, and requests
   that arrive while others are on the GPU join the next batch as soon as a
   worker frees up; large requests run one per call, enqueued in arrival order
   on one large-request stream as soon as they arrive, so that they follow each
@@ -143,23 +143,24 @@ class Server:
     """Continuous-batching server of labelling requests on one GPU.
 
     Workers are library contexts, each on its own stream, above the producers'
-    priority; `small_workers` of them run at a still higher priority and take
-    only small requests (at most `small_sites` sites), batched together up to
-    `max_batch` requests and `small_batch_sites` sites, so that a small request
-    never waits behind a large one and its kernels are scheduled ahead of a large
-    call already on the GPU.  The first of the other workers takes every large
-    request, one per call, in arrival order: it is a queue on its stream, each
-    call enqueued when its request arrives, so that a large request waits only
-    for the large ones before it, as in FIFO, but for none of the small ones.
-    Workers with nothing in flight take small batches when no small worker is
-    free.  The FIFO baseline is every request on the large-request stream.
+    priority; `small_workers` of them take only small requests (at most
+    `small_sites` sites), batched together up to `max_batch` requests and
+    `small_batch_sites` sites, so that a small request never waits behind a large
+    one.  The first of the other workers takes every large request, one per call,
+    in arrival order: it is a queue on its stream, each call enqueued when its
+    request arrives, so that a large request waits only for the large ones before
+    it, as in FIFO, but for none of the small ones.  Its stream has the highest
+    priority, so that the small batches running beside a large call delay it as
+    little as possible (the latency tail is the large requests').  Workers with
+    nothing in flight take small batches when no small worker is free.  The FIFO
+    baseline is every request on the large-request stream.
     """
 
     def __init__(self, device: int = 0, cap_bytes: int = 32 * GB, workers: int = 4, max_batch: int = 64,
                  max_batch_sites: int = 1 << 28, tile: tuple | None = None, graphs: bool = False,
                  producers: int = 4, small_workers: int = 2, small_sites: int = 1 << 21,
-                 small_batch_sites: int = 1 << 23, small_priority: int = -2,
-                 large_priority: int = -1, max_side: int = 512):
+                 small_batch_sites: int = 1 << 23, small_priority: int = -1,
+                 large_priority: int = -2, max_side: int = 512):
         import torch
         self.device = device
         self.cap = cap_bytes
@@ -170,7 +171,7 @@ class Server:
         self.n_small = max(0, min(small_workers, workers - 1))
         # Priorities (a lower number is a higher one, clamped to the device's range): the
         # simulation stand-in's producers run at the default, every labelling worker above
-        # them, and the small-request workers above the large ones.
+        # them, and the large-request worker above the small ones.
         self.producers = [torch.cuda.Stream(device=device) for _ in range(producers)]
         self.streams = ([torch.cuda.Stream(device=device, priority=small_priority) for _ in range(self.n_small)] +
                         [torch.cuda.Stream(device=device, priority=large_priority) for _ in range(workers - self.n_small)])
