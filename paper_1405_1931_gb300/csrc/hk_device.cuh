@@ -302,15 +302,16 @@ __device__ __forceinline__ int s_find_ro(const int *par, int x) {
     return x;
 }
 
-// find with path halving (during the unions)
+// find with path splitting (during the unions): every node passed is pointed at its
+// grandparent, an ancestor, so concurrent finds and links stay valid
 __device__ __forceinline__ int s_find(int *par, int x) {
     int p = par[x];
     while (p != x) {
         const int gp = par[p];
         if (gp == p) return p;
         par[x] = gp;
-        x = gp;
-        p = par[x];
+        x = p;
+        p = gp;
     }
     return x;
 }

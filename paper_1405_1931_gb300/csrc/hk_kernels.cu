@@ -326,7 +326,8 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
 
         // y- and z-neighbours: one union per overlapping run pair of rows (y-1, y) and
         // (z-1, z).  Both pair lists come from one scan of packed counts (each total
-        // is at most 16 * R < 2^16) and normally share one pass of unions.
+        // is at most 16 * R < 2^16) and normally share one pass of unions, the z pairs
+        // listed first (measured faster than y first).
         const uint32_t osy = ly > 0 ? run_starts(m & S.m[r - 1]) : 0u;
         const uint32_t osz = lz > 0 ? run_starts(m & S.m[r - TY]) : 0u;
         int tot_packed;
@@ -353,8 +354,8 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
             }
         };
         if (ny_tot + nz_tot <= CAP) {           // block-uniform
-            if (osy) write_pairs(osy, r - 1, packed & 0xffff);
-            if (osz) write_pairs(osz, r - TY, ny_tot + (packed >> 16));
+            if (osz) write_pairs(osz, r - TY, packed >> 16);
+            if (osy) write_pairs(osy, r - 1, nz_tot + (packed & 0xffff));
             __syncthreads();
             union_pairs(ny_tot + nz_tot);
             __syncthreads();
