@@ -75,15 +75,15 @@ def dist_env():
 # taken on, identified by TRAFFIC_SOURCE_SHA; after any change to them it is reported
 # as null.
 TRAFFIC_SITES = 512 ** 3
-TRAFFIC_BYTES = {"occupancy": 554.1e6, "tile_label": 61.8e6, "face_merge": 37.1e6, "piece_finalize": 30.0e6,
-                 "scan": 8.5e6, "lattice_finish": 0.0, "flatten": 630.9e6}
-TRAFFIC_SOURCE_SHA = "10844f792db9d060"
+TRAFFIC_BYTES = {"occupancy": 554.3e6, "tile_label": 62.0e6, "face_merge": 37.2e6, "piece_finalize": 30.0e6,
+                 "scan": 8.5e6, "lattice_finish": 0.0, "flatten": 630.4e6}
+TRAFFIC_SOURCE_SHA = "a4c2ddd50799fc01"
 # Warp instructions of one launch of the two instruction-bound passes at 512^3
 # (smsp__inst_executed.sum of one ncu capture of these kernel sources), scaled by
 # sites like the traffic and held to the same kernel sources.  Their roofline is the
 # issue rate: 4 warp schedulers per SM, each issuing at most one warp instruction per
 # clock.
-INST_PER_LAUNCH = {"tile_label": 341903769, "flatten": 193651326}
+INST_PER_LAUNCH = {"tile_label": 340981944, "flatten": 169020761}
 
 
 # the sources of the passes of one hk_label call and of their launch (the captures above

@@ -202,15 +202,15 @@ __device__ __forceinline__ TileGeo tile_geo(const LatDev &L, int64_t t) {
 __device__ __forceinline__ bool occupied(float v, int mode) { return mode ? (v < -0.5f) : (v > 0.0f); }
 
 __device__ __forceinline__ uint32_t run_starts(uint32_t m) { return m & ~(m << 1); }
+// the last site of every run: bit x set when x is occupied and x + 1 is not (or x = 31)
+__device__ __forceinline__ uint32_t run_ends(uint32_t m) { return m & ~(m >> 1); }
 // bits 0..x set
 __device__ __forceinline__ uint32_t le_mask(int x) { return (2u << x) - 1u; }
 // run id (within the tile) of occupied site x of a row with run starts rs
 __device__ __forceinline__ int run_of(int rbase, uint32_t rs, int x) { return rbase + __popc(rs & le_mask(x)) - 1; }
-// length of the run starting at bit x0 of m
-__device__ __forceinline__ int run_len(uint32_t m, int x0) {
-    const uint32_t v = m >> x0;
-    return (v == 0xffffffffu) ? 32 : __ffs(~v) - 1;
-}
+// length of the run starting at bit x0 of m: the first run end at or above x0, which
+// __ffs counts from 1
+__device__ __forceinline__ int run_len(uint32_t m, int x0) { return __ffs(run_ends(m) >> x0); }
 
 // ---- PTX helpers ----------------------------------------------------------------------
 // Programmatic dependent launch: the kernels of the labelling sequence are launched so

@@ -19,6 +19,7 @@
 //                     in label order and the histogram.
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 
 #include "hk_device.cuh"
 #include "hk_launch.h"
@@ -977,50 +978,61 @@ k_flatten(const __grid_constant__ LatBatch<NL> B, const __grid_constant__ TmapBa
         }
 
         // a4-a7: one pass over the runs of each row in x order: cluster roots get
-        // their rank, size and histogram entry; every run writes its label
+        // their rank, size and histogram entry; every run writes its label.  The loop
+        // is compiled for each case of two tile-uniform conditions, so that neither is
+        // tested per run: PF, the codes and piece records arrived by bulk copy (else
+        // they are read from global memory); BIG, the tile has boundary pieces beyond
+        // the staged ones (read from global memory).
         int64_t rank = (int64_t)(uint32_t)(pre_row - pre_lat);
         const int site_row = ((g.z0 + lz) * L.ny + (g.y0 + ly)) * L.nx + g.x0;
         const int site_row0 = (g.z0 * L.ny + g.y0) * L.nx + g.x0, sxy_i = L.nx * L.ny;
         uint32_t rootbits = 0;                // first sites of cluster roots in this row
         const int soff = SLAB ? (int)W.site_off : 0;   // labels of a slab are sites of the whole lattice
-        uint32_t w = rs;
-        int id = rb;
-        while (w) {
-            const int x0 = __ffs(w) - 1;
-            w &= w - 1;
-            const int c = prefetch ? (int)S.codes[id] : (int)__ldg(C + id);
-            ++id;
-            const int k = c & CODE_LOW;
-            const bool isb = (c & CODE_BOUNDARY) != 0, isr = (c & CODE_ROOT) != 0;
-            const int kk = k < FlatSmem<TY, TZ>::GL ? k : 0;
-            int gl = S.gl[kk], gs = S.gsize[kk];
-            if (isb && k >= FlatSmem<TY, TZ>::GL) {
-                gl = __ldg(W.key + base + k);
-                gs = __ldg(W.psize + base + k);
-            }
-            // all three labels are formed and one is selected (no divergent branches)
-            const int ci = (isb || isr) ? 0 : c;   // an interior non-root run: its root's position
-            const int crow = ci >> 5;
-            const int own = site_row + x0;
-            const int other = site_row0 + (crow / TY) * sxy_i + (crow % TY) * L.nx + (ci & 31);
-            const int lab = SLAB ? (isb ? gl : (isr ? own : other)) + soff : (isb ? gl : (isr ? own : other));
-            const int size = isr ? (isb ? gs : k) : -1;
-            if (size > 0) {
-                if (rank < L.sizes_cap) {
-                    L.sizes[rank] = size;
-                    if (SLAB) W.roots[rank] = lab;
+        const uint32_t re = run_ends(m);
+        auto run_loop = [&](auto PF, auto BIG) {
+            constexpr bool pf = decltype(PF)::value, big = decltype(BIG)::value;
+            uint32_t w = rs;
+            int id = rb;
+            while (w) {
+                const int x0 = __ffs(w) - 1;
+                w &= w - 1;
+                const int c = pf ? (int)S.codes[id] : (int)__ldg(C + id);
+                ++id;
+                const int k = c & CODE_LOW;
+                const bool isb = (c & CODE_BOUNDARY) != 0, isr = (c & CODE_ROOT) != 0;
+                const int kk = k < FlatSmem<TY, TZ>::GL ? k : 0;
+                int gl = S.gl[kk], gs = S.gsize[kk];
+                if (big && isb && k >= FlatSmem<TY, TZ>::GL) {
+                    gl = __ldg(W.key + base + k);
+                    gs = __ldg(W.psize + base + k);
                 }
-                ++rank;
-                rootbits |= 1u << x0;
-                atomicAdd(&S.hist[31 - __clz(size)], 1);
-            }
-            const int xe = x0 + run_len(m, x0);
-            int *row = S.stage + r * 32;
-            const int sw = (r & 7) << 2;
-            row[x0 ^ sw] = lab;
+                // all three labels are formed and one is selected (no divergent branches)
+                const int ci = (isb || isr) ? 0 : c;   // an interior non-root run: its root's position
+                const int crow = ci >> 5;
+                const int own = site_row + x0;
+                const int other = site_row0 + (crow / TY) * sxy_i + (crow % TY) * L.nx + (ci & 31);
+                const int lab = SLAB ? (isb ? gl : (isr ? own : other)) + soff : (isb ? gl : (isr ? own : other));
+                const int size = isr ? (isb ? gs : k) : -1;
+                if (size > 0) {
+                    if (rank < L.sizes_cap) {
+                        L.sizes[rank] = size;
+                        if (SLAB) W.roots[rank] = lab;
+                    }
+                    ++rank;
+                    rootbits |= 1u << x0;
+                    atomicAdd(&S.hist[31 - __clz(size)], 1);
+                }
+                const int xe = x0 + __ffs(re >> x0);   // one past the run's last site
+                int *row = S.stage + r * 32;
+                const int sw = (r & 7) << 2;
+                row[x0 ^ sw] = lab;
 #pragma unroll 1
-            for (int x = x0 + 1; x < xe; ++x) row[x ^ sw] = lab;
-        }
+                for (int x = x0 + 1; x < xe; ++x) row[x ^ sw] = lab;
+            }
+        };
+        if (!prefetch) run_loop(std::false_type{}, std::true_type{});
+        else if (nb > FlatSmem<TY, TZ>::GL) run_loop(std::true_type{}, std::true_type{});
+        else run_loop(std::true_type{}, std::false_type{});
         if (L.inside && ly <= g.lastY && lz <= g.lastZ)   // index fields: ranks of any root, later
             W.rootbits[L.seg0 + ((int64_t)(g.z0 + lz) * L.ny + (g.y0 + ly)) * L.nbx + g.bx] = rootbits;
         if (use_tma) fence_proxy_async();
