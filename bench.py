@@ -75,15 +75,15 @@ def dist_env():
 # taken on, identified by TRAFFIC_SOURCE_SHA; after any change to them it is reported
 # as null.
 TRAFFIC_SITES = 512 ** 3
-TRAFFIC_BYTES = {"occupancy": 554.3e6, "tile_label": 62.0e6, "face_merge": 37.2e6, "piece_finalize": 30.0e6,
-                 "scan": 8.5e6, "lattice_finish": 0.0, "flatten": 630.4e6}
-TRAFFIC_SOURCE_SHA = "a4c2ddd50799fc01"
+TRAFFIC_BYTES = {"occupancy": 554.3e6, "tile_label": 61.9e6, "face_merge": 37.3e6, "piece_finalize": 30.1e6,
+                 "scan": 8.5e6, "lattice_finish": 0.0, "flatten": 630.2e6}
+TRAFFIC_SOURCE_SHA = "2a066ea8b3ba4896"
 # Warp instructions of one launch of the two instruction-bound passes at 512^3
 # (smsp__inst_executed.sum of one ncu capture of these kernel sources), scaled by
 # sites like the traffic and held to the same kernel sources.  Their roofline is the
 # issue rate: 4 warp schedulers per SM, each issuing at most one warp instruction per
 # clock.
-INST_PER_LAUNCH = {"tile_label": 340981944, "flatten": 169020761}
+INST_PER_LAUNCH = {"tile_label": 340986233, "flatten": 169021401}
 
 
 # the sources of the passes of one hk_label call and of their launch (the captures above
@@ -455,8 +455,8 @@ def extra_configs(args, peak):
     gra = timed(lambda: lab.label_batched(items, stream=s))
     lab.set_graphs(False)
     lab.sync_status(s)
-    lab.set_tile(16, 16)
-    lab.set_merge(2, 1)
+    lab.set_tile(16, 16)   # the library's defaults again
+    lab.set_merge(1, 1)
     # compulsory bytes of the whole batch: 8 B a site, 8 B a cluster size, 256 B of histogram a lattice
     nclus = sum(int(o[3].item()) for _, _, o in items)
     bbytes = 8 * sites + 8 * nclus + 256 * len(items)

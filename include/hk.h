@@ -376,7 +376,7 @@ int hk_set_tile(hk_ctx *ctx, int ty, int tz);
  * schedule; only the time differs):
  *   unions_per_lane  face merge: unions each lane takes per step, their find chains
  *                    walked in lockstep so their loads overlap: 1, 2 or 4 (0 = the
- *                    default, 2);
+ *                    default, 1);
  *   combine_hot      piece finalize: 1 (default) combines the size additions of the
  *                    cluster root that collects most of them -- the percolating
  *                    cluster's -- per warp and per CTA before the global add; 0 adds

@@ -26,7 +26,7 @@ from . import hk
 
 TILES = ((8, 8), (16, 8), (16, 16), (32, 8))
 MERGES = ((1, 1), (2, 1), (4, 1), (1, 0), (2, 0), (4, 0))   # (face-merge unions per lane, combine hot root)
-DEFAULT_MERGE = (2, 1)
+DEFAULT_MERGE = (1, 1)   # the library default
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "hk_autotune.json")
 
 

@@ -796,7 +796,7 @@ int hk_set_graphs(hk_ctx *ctx, int enable) {
 
 int hk_set_merge(hk_ctx *ctx, int unions_per_lane, int combine_hot) {
     if (!ctx) return HK_ERR_ARG;
-    if (unions_per_lane == 0) unions_per_lane = 2;
+    if (unions_per_lane == 0) unions_per_lane = 1;
     if (unions_per_lane != 1 && unions_per_lane != 2 && unions_per_lane != 4) return HK_ERR_ARG;
     if (combine_hot != 0 && combine_hot != 1) return HK_ERR_ARG;
     ctx->merge.unions = unions_per_lane;

@@ -576,15 +576,20 @@ k_tile_label(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
 // merge-schedule parameter: 1, 2 or 4) and
 // walks the finds of all their endpoints in lockstep, so their loads are in flight
 // together; the roots are then linked by CAS, and a lost CAS falls back to g_union.
+// CTAs of FM_WARPS warps: a CTA's resources return only when its slowest warp (longest
+// parent chain) is done, so small CTAs keep more warps waiting on loads in flight
+// (32 CTAs of 2 warps still fill an SM).
 // --------------------------------------------------------------------------------------
+constexpr int FM_WARPS = 2;
+constexpr int PF_WARPS = 4;
 template <int TY, int TZ, int NL, int U>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(32 * FM_WARPS)
 k_face_merge(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
     grid_dep_wait();
     using SH = TileShape<TY, TZ>;
     constexpr int C = 2 * U;   // U unions, 2 U find chains per lane and step
     const int lane = threadIdx.x & 31;
-    const int64_t t = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int64_t t = (int64_t)blockIdx.x * FM_WARPS + (threadIdx.x >> 5);
     if (t >= ntiles) return;
     const LatDev &L = B.lat[(NL == 1) ? 0 : find_lattice(B.lat, B.n, t)];
     const TileGeo g = tile_geo<TY, TZ>(L, t);
@@ -656,15 +661,16 @@ k_face_merge(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
 // K3: piece finalize (one warp per tile, one piece per lane).  Size additions into
 // the same cluster root are combined per group of lanes; with HOT (a merge-schedule
 // parameter) the root that collects most of them -- the percolating cluster's -- is
-// further combined per warp and per CTA, because it collects pieces from most tiles.
+// further combined per warp and per CTA of PF_WARPS warps, because it collects pieces
+// from most tiles.
 // --------------------------------------------------------------------------------------
 template <int NL, bool HOT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(32 * PF_WARPS)
 k_piece_finalize(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles) {
     grid_dep_wait();
-    __shared__ int hot_target[8];   // per warp: the cluster root its pieces fed most, and the sum
-    __shared__ int hot_sum[8];
-    const int64_t t = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    __shared__ int hot_target[PF_WARPS];   // per warp: the cluster root its pieces fed most, and the sum
+    __shared__ int hot_sum[PF_WARPS];
+    const int64_t t = (int64_t)blockIdx.x * PF_WARPS + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     // The root that collects most sizes (the percolating cluster's, above all) is added
     // once per warp and then once per CTA; other roots once per group of lanes.
@@ -718,12 +724,12 @@ k_piece_finalize(const __grid_constant__ LatBatch<NL> B, Work W, int64_t ntiles)
         hot_sum[wid] = hot_acc;
     }
     __syncthreads();
-    if (threadIdx.x < 8) {   // one add per distinct hot root of the CTA
+    if (threadIdx.x < PF_WARPS) {   // one add per distinct hot root of the CTA
         const int h = hot_target[threadIdx.x];
         if (h >= 0) {
             bool first = true;
             int s = 0;
-            for (int w = 0; w < 8; ++w)
+            for (int w = 0; w < PF_WARPS; ++w)
                 if (hot_target[w] == h) {
                     if (w < (int)threadIdx.x) first = false;
                     s += hot_sum[w];
@@ -1442,13 +1448,14 @@ static cudaError_t launch_all(const LatDev *lats, int n, const Plan &P, const Wo
     launch_dep(k_tile_label<TY, TZ, NL, false>, (unsigned)(P.ntiles < grid1b ? P.ntiles : grid1b), SH::NT, smem1b, st,
                B, W, P.ntiles);
     mark(2);
-    const unsigned gm = (unsigned)((P.ntiles + 7) / 8);
-    if (ms.unions == 1) launch_dep(k_face_merge<TY, TZ, NL, 1>, gm, 256, 0, st, B, W, P.ntiles);
-    else if (ms.unions == 4) launch_dep(k_face_merge<TY, TZ, NL, 4>, gm, 256, 0, st, B, W, P.ntiles);
-    else launch_dep(k_face_merge<TY, TZ, NL, 2>, gm, 256, 0, st, B, W, P.ntiles);
+    const unsigned gfm = (unsigned)((P.ntiles + FM_WARPS - 1) / FM_WARPS);
+    if (ms.unions == 1) launch_dep(k_face_merge<TY, TZ, NL, 1>, gfm, 32 * FM_WARPS, 0, st, B, W, P.ntiles);
+    else if (ms.unions == 4) launch_dep(k_face_merge<TY, TZ, NL, 4>, gfm, 32 * FM_WARPS, 0, st, B, W, P.ntiles);
+    else launch_dep(k_face_merge<TY, TZ, NL, 2>, gfm, 32 * FM_WARPS, 0, st, B, W, P.ntiles);
     mark(3);
-    if (ms.hot) launch_dep(k_piece_finalize<NL, true>, gm, 256, 0, st, B, W, P.ntiles);
-    else launch_dep(k_piece_finalize<NL, false>, gm, 256, 0, st, B, W, P.ntiles);
+    const unsigned gpf = (unsigned)((P.ntiles + PF_WARPS - 1) / PF_WARPS);
+    if (ms.hot) launch_dep(k_piece_finalize<NL, true>, gpf, 32 * PF_WARPS, 0, st, B, W, P.ntiles);
+    else launch_dep(k_piece_finalize<NL, false>, gpf, 32 * PF_WARPS, 0, st, B, W, P.ntiles);
     mark(4);
     const int64_t nb = (P.nrows + SCAN_CH) / SCAN_CH;   // covers index nrows (the total)
     launch_dep(k_scan_reduce<NL>, (unsigned)nb, SCAN_NT, 0, st, B, (const uint8_t *)W.cnt, P.nrows, W.bsum);

@@ -104,7 +104,7 @@ cudaError_t launch_small(const LatDev *lats, int n, int32_t *status, int32_t loc
 // whether the piece finalize combines the size additions of the cluster root that
 // collects most of them per warp and per CTA (hot) or adds each group's directly.
 struct MergeSchedule {
-    int unions = 2;
+    int unions = 1;
     int hot = 1;
 };
 

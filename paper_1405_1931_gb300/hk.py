@@ -309,7 +309,7 @@ class Labeller:
         self.device = int(device)
         self.ctx = hk_create(self.device)
         self.tile = (16, 16)
-        self.merge = (2, 1)
+        self.merge = (1, 1)
         if tile is not None:
             self.set_tile(*tile)
 
@@ -335,12 +335,12 @@ class Labeller:
         if rc != HK_OK:
             raise HKError(rc, "hk_set_graphs")
 
-    def set_merge(self, unions_per_lane: int = 2, combine_hot: int = 1):
+    def set_merge(self, unions_per_lane: int = 1, combine_hot: int = 1):
         """Merge schedule of the tiled passes (face-merge unions per lane, hot-root combining)."""
         rc = hk_set_merge(self.ctx, unions_per_lane, combine_hot)
         if rc != HK_OK:
             raise HKError(rc, "hk_set_merge")
-        self.merge = (unions_per_lane or 2, combine_hot)
+        self.merge = (unions_per_lane or 1, combine_hot)
 
     def set_small_path(self, enable=True):
         """One-launch kernels for small lattices: True/1 the library picks (default), False/0
