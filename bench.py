@@ -800,7 +800,23 @@ def main():
         e2e["link_gbs"] = {"h2d": rate(lambda: d_in.copy_(h_in, non_blocking=True), 4 * nb),
                            "d2h": rate(lambda: h_out.copy_(d_out, non_blocking=True), 4 * nb),
                            "duplex_each_way": rate(both, 4 * nb)}
+        # the same on the whole buffers the steps use: phi in, and each context's labels
+        # out while phi comes in (the pattern of the pipelined steps), one pass each
         del d_in
+        d_big = torch.empty(N, dtype=torch.float32, device="cuda")
+        whole = {"h2d_phi": rate(lambda: d_big.copy_(phi_h.reshape(-1), non_blocking=True), 4 * N, reps=1)}
+        for j, o in enumerate(outs_h):
+            h_lab = o[0].reshape(-1).view(torch.float32)
+
+            def pair(h_lab=h_lab):
+                with torch.cuda.stream(streams[0]):
+                    d_big.copy_(phi_h.reshape(-1), non_blocking=True)
+                with torch.cuda.stream(streams[-1]):
+                    h_lab.copy_(phi.reshape(-1), non_blocking=True)
+            whole[f"d2h_labels{j}"] = rate(lambda h_lab=h_lab: h_lab.copy_(phi.reshape(-1), non_blocking=True), 4 * N, reps=1)
+            whole[f"duplex_phi_labels{j}_each_way"] = rate(pair, 4 * N, reps=1)
+        e2e["link_gbs"]["whole_buffers"] = whole
+        del d_big
         for m in more:
             m.close()
         del phi_h, outs_h
