@@ -51,3 +51,20 @@ def test_reference_arm_runs_on_rank_zero_only(capsys):
         steps, warmup, gpus = 1, 0, 2
     bench.run_reference(Args, rank=1, world=2)
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_on_rank_zero(capsys):
+    """The reference arm's JSON line: the oracle timed on the host on a bounded sample,
+    with the metric, unit and direction of the GPU arm and its own cpu_baseline and e2e."""
+    import json
+
+    class Args:
+        steps, warmup, gpus = 1, 0, 1
+    bench.run_reference(Args, rank=0, world=1)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["unit"] == "Gsites/s" and line["higher_is_better"] is True and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "Gsites/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert line["steps"] == 1 and line["n_gpus"] == 1
